@@ -1,0 +1,405 @@
+"""Throughput benchmark of the fused phonon-LBM stream-collide step.
+
+Workload: 8192 x 8192 fully periodic D2Q8 lattice, sine temperature mode of
+wavelength 512 cells plus seeded U[-1e-6, 1e-6) noise, Kn_N = 0.01,
+Kn_R = 0.1 measured on the 512-cell wavelength, populations stored as FP32
+deviations (``--precision`` selects fp16/bf16/fp64 storage).  One bench
+step = one time step of Eq. 13 over the whole lattice (pull-stream, seam and
+wall rules, collision); the FP64 residual / energy reduction runs every 100
+steps inside the timed region.  The population buffers (2 x 2.1 GB) exceed
+the 129 MB L2, so no flush is needed between steps.
+
+Metric: GLUPS (10^9 lattice-site updates per second, whole job).  Also
+reported: the roofline of the stream-collide kernel (algorithmic bytes
+16 x sizeof(storage) per site update over its CUDA-event time), an
+end-to-end figure through the public API with host buffers, and the FP64
+oracle on the host cores as a CPU baseline.
+
+Multi-GPU: ``--gpus N`` (under torchrun) runs N independent replicas, one
+lattice per rank, with no data-path collective (weak scaling); the job time
+is the maximum over ranks.
+
+``--impl reference`` times the FP64 CPU oracle instead (host cores, bounded
+sample of the same workload), rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2010_01847_gb300 import inputs  # noqa: E402
+
+RESIDUAL_EVERY = 100
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "GLUPS & % HBM roofline; time-to-steady-state, warm-started vs plain LBM"
+STORAGE_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp64": 8}
+DTYPE = {"fp32": "f32", "fp16": "f32", "bf16": "f32", "fp64": "f64"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=list(STORAGE_BYTES))
+    ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--nx", type=int, default=inputs.THROUGHPUT_8192.nx)
+    ap.add_argument("--ny", type=int, default=inputs.THROUGHPUT_8192.ny)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(args):
+    w = inputs.THROUGHPUT_8192
+    return dict(nx=args.nx, ny=args.ny, kn_N=w.kn_N, kn_R=w.kn_R, length=w.length)
+
+
+def cpu_info():
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        m = re.search(r"Model name:\s*(.+)", out)
+        model = m.group(1).strip() if m else ""
+    except Exception:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_sample(w, seconds: float):
+    """Time the FP64 oracle on a bounded sample of the workload: a periodic
+    2048 x 2048 window of the same fields, as many steps as fit ~`seconds`."""
+    import oracle
+    cores, model = cpu_info()
+    oracle.set_threads(cores)
+    side = min(2048, w["nx"], w["ny"])
+    tau_N = oracle.tau_from_kn(w["kn_N"], w["length"])
+    tau_R = oracle.tau_from_kn(w["kn_R"], w["length"])
+    e = inputs.sine_mode(side, side, 512.0, 1e-3, noise=1e-6)
+    lat = oracle.run(side, side, tau_N, tau_R, e)
+    t0 = time.perf_counter()
+    lat.step(1)
+    one = time.perf_counter() - t0
+    steps = max(1, int(seconds / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    lat.step(steps)
+    dt = time.perf_counter() - t0
+    glups = side * side * steps / dt / 1e9
+    return {"value": glups, "unit": "GLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{side}x{side} periodic window of the workload, {steps} steps, "
+                      f"{dt:.1f} s, FP64, host '{model}'"}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if key in d:
+                v = d[key]
+                v = v.get("value", v) if isinstance(v, dict) else v
+                return float(v), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2010_01847_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_name, precision, nx, ny):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        f = line.split()
+        if len(f) < 7 or f[0].startswith("#"):
+            continue
+        kname, prec, snx, sny, nbytes, shash = f[0], f[1], int(f[2]), int(f[3]), float(f[4]), f[5]
+        if kname == kernel_name and prec == precision and shash == src:
+            return nbytes * (nx * ny) / (snx * sny)   # traffic grows with the sites
+    return None
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores, each bench step one timed oracle
+    step on a periodic window of the workload sized so the whole run stays
+    within about 90 s.  Rank 0 only."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    w = workload(args)
+    cores, model = cpu_info()
+    oracle.set_threads(cores)
+    tau_N = oracle.tau_from_kn(w["kn_N"], w["length"])
+    tau_R = oracle.tau_from_kn(w["kn_R"], w["length"])
+    cal = oracle.run(512, 512, tau_N, tau_R, inputs.sine_mode(512, 512, 512.0, 1e-3, noise=1e-6))
+    t0 = time.perf_counter()
+    cal.step(2)
+    rate = 2 * 512 * 512 / (time.perf_counter() - t0)
+    budget = min(args.cpu_seconds, 90.0 / max(args.steps + args.warmup, 1))
+    side = int(min(2048, max(64, math.sqrt(rate * budget))) // 64 * 64)
+    side = min(side, w["nx"], w["ny"])
+    lat = oracle.run(side, side, tau_N, tau_R, inputs.sine_mode(side, side, 512.0, 1e-3,
+                                                                noise=1e-6))
+    lat.step(max(args.warmup, 0))
+    total = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        lat.step(1)
+        total += time.perf_counter() - t0
+    value = side * side * args.steps / total / 1e9
+    sample = {"value": value, "unit": "GLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+              "sample": f"{side}x{side} periodic window of the workload, {args.steps} timed "
+                        f"steps ({total:.1f} s), FP64, host '{model}'"}
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": w["nx"] * w["ny"] / (value * 1e9) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"heat_mode_{w['nx']}x{w['ny']}", "kn_N": w["kn_N"],
+                   "kn_R": w["kn_R"], "storage": "fp64 (oracle)", "lattice": "D2Q8"},
+        "cpu_baseline": sample,
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+    import paper_2010_01847_gb300 as plbm
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = workload(args)
+    nx, ny = w["nx"], w["ny"]
+    tau_N = plbm.tau_from_kn(w["kn_N"], w["length"])
+    tau_R = plbm.tau_from_kn(w["kn_R"], w["length"])
+    e = inputs.sine_mode(nx, ny, 512.0, 1e-3, noise=1e-6)
+    e_dev = torch.from_numpy(e).to(dev)
+    z_dev = torch.zeros_like(e_dev)
+
+    lat = plbm.Lattice(nx, ny, tau_N, tau_R, precision=args.precision, kernel=args.kernel)
+    lat.init(e_dev, z_dev, z_dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def chunked(nsteps, events=None):
+        """Advance nsteps with the residual every RESIDUAL_EVERY steps;
+        record events around each run of stream-collide launches."""
+        done = 0
+        launches = 0
+        while done < nsteps:
+            k = min(RESIDUAL_EVERY, nsteps - done)
+            if events is not None:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            lat.step(k)
+            if events is not None:
+                b.record(stream)
+                events.append((a, b, k))
+            launches += k
+            done += k
+            if done % RESIDUAL_EVERY == 0:
+                lat.residual()
+                launches += 2
+        return launches
+
+    chunked(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    events = []
+    sampler = ClockSampler(dev.index)
+    with sampler:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        launches = chunked(args.steps, events)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    kern_s = sum(a.elapsed_time(b) for a, b, _ in events) / 1e3
+    kern_steps = sum(k for _, _, k in events)
+    if dist:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = t.item()
+    sites = nx * ny
+    value = world * sites * args.steps / elapsed / 1e9
+
+    # roofline of the stream-collide kernel
+    bps = 16 * STORAGE_BYTES[args.precision]
+    avg_launch = kern_s / kern_steps
+    achieved = bps * sites / avg_launch / 1e9
+    peak, peak_kind = measured_peak()
+    kname = "step_" + lat.kernel
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(kname, args.precision, nx, ny),
+            "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else 'profiling-recipe fallback 6.8 TB/s'})",
+            "kernel": kname, "bytes_per_site_update": bps,
+            "avg_launch_us": avg_launch * 1e6}
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(a).pin_memory() for a in (e, np.zeros_like(e), np.zeros_like(e))]
+        out = [torch.empty((ny, nx), dtype=torch.float64).pin_memory() for _ in range(3)]
+        hp = [h.numpy() for h in host]
+        op = [o.numpy() for o in out]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t_start = time.perf_counter()
+        lat.init(*hp)
+        chunked(args.steps)
+        m = lat.moments()
+        for dst, src in zip(op, m):
+            dst[...] = src
+        t_e2e = time.perf_counter() - t_start
+        if dist:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = t.item()
+        e2e = {"value": world * sites * args.steps / t_e2e / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": 3 * 8 * sites / args.steps,
+               "d2h_bytes_per_step": 3 * 8 * sites / args.steps,
+               "what": "lbm_init from pinned host (e, qx, qy) + steps + lbm_moments to host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(w, args.cpu_seconds)
+
+    if rank == 0:
+        clocks = sampler.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"heat_mode_{nx}x{ny}", "lattice": "D2Q8 (paper's D2Q9 "
+                       "label: rest population identically zero, not stored)",
+                       "kn_N": w["kn_N"], "kn_R": w["kn_R"], "length_cells": w["length"],
+                       "storage": f"{args.precision} deviation" if args.precision != "fp64"
+                       else "fp64 deviation", "kernel": lat.kernel,
+                       "residual_every": RESIDUAL_EVERY,
+                       "l2": "inputs larger than L2 (2 x population buffers >> 129 MB); "
+                             "no flush", "parallelism": f"replicas x{world}"},
+            "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+            "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

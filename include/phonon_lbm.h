@@ -1,0 +1,214 @@
+/*
+ * phonon_lbm.h - C-ABI of the GB300 (sm_103a) phonon lattice Boltzmann solver.
+ *
+ * The solver advances the lattice Boltzmann equation of Guo & Wang for the
+ * phonon Boltzmann equation under Callaway's dual relaxation model
+ * (arXiv 2010.01847, Section 2), on a 2-D D2Q8 lattice:
+ *
+ *   e_i(x + c_i, t + 1) - e_i(x, t) = (e_i^eq - e_i)/tau + S_i        (Eq. 13)
+ *   e_i^eq = w_i e + 5 a_i (c_i . q) / 3                              (Eq. 15)
+ *   S_i    = -(1 - 1/(2 tau)) 5 a_i (c_i . q) / (3 tau_r)             (Eq. 16)
+ *   e = sum_i e_i (Eq. 53),  q = 2 tau_r/(2 tau_r + 1) sum_i c_i e_i  (Eq. 54)
+ *   tau = tau_C + 1/2, 1/tau_C = 1/tau_N + 1/tau_R, tau_r = tau_R     (Eq. 49)
+ *
+ * with w_i, a_i of Eqs. 17-18, in lattice units (dx = dt = c = 1, so
+ * v_g = sqrt(5/3) by Eq. 48).  Directions i = 0..7 are the paper's 1..8:
+ * (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
+ *
+ * Boundaries (Section 2.5): periodic wrap; the periodic temperature-gradient
+ * condition along x (Eqs. 59-60: populations crossing the x seam from
+ * x = nx-1 to x = 0 gain w_i delta_e, those crossing back lose it); diffuse
+ * adiabatic walls on the rows y = 0 and y = ny-1 (Eq. 58: the unknown
+ * populations of a wall node are w_i / (5/18) times the sum of its incident
+ * ones).  Walls sit on the boundary nodes; they act right after streaming;
+ * wall nodes then collide like every other node.
+ *
+ * STATE CONTRACT.  "The state at step n" is the set of populations after
+ * streaming and boundary treatment of step n, before collision.  lbm_init
+ * sets step 0 to the equilibrium of Eq. 15; lbm_moments and lbm_residual
+ * report e and q of the state at the current step.
+ *
+ * Conventions for every call:
+ *   - Every call returns an lbm_status; nothing throws across the ABI.  The
+ *     text of the last failure is lbm_last_error(ctx) (ctx may be NULL for a
+ *     failed lbm_create).
+ *   - Arguments are checked before any work is queued.
+ *   - Host arrays are row-major [ny][nx], index y*nx + x, float64.
+ *   - Device pointers are CUDA device addresses on the context's device.
+ *   - Calls queue work on the context's stream.  "async" calls return once
+ *     the work is queued; a fault inside a kernel is reported by the next
+ *     call that synchronises (lbm_sync, lbm_moments, lbm_residual, ...).
+ *   - A context is not thread-safe; one host thread drives it at a time.
+ */
+#ifndef PHONON_LBM_H
+#define PHONON_LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,        /* an argument is out of range or NULL           */
+    LBM_ENOMEM = 2,        /* a device allocation failed                    */
+    LBM_ECUDA = 3,         /* a CUDA call or kernel failed                  */
+    LBM_ENONFINITE = 4,    /* the state holds NaN or Inf                    */
+    LBM_ETIMEOUT = 5,      /* a bounded device-side wait gave up            */
+    LBM_EUNSUPPORTED = 6   /* a valid request this build does not support   */
+} lbm_status;
+
+typedef enum {
+    LBM_BC_PERIODIC = 0,            /* plain wrap                              */
+    LBM_BC_PERIODIC_GRADIENT = 1,   /* Eqs. 59-60; x direction only            */
+    LBM_BC_DIFFUSE_WALLS = 2        /* Eq. 58 on rows 0 and ny-1; y only       */
+} lbm_bc;
+
+/* How the populations are stored in device memory.  All but LBM_FP64 store
+ * the deviation d_i = s (e_i - w_i e_ref) from the equilibrium at rest at the
+ * reference energy e_ref, with s = 1 for LBM_FP32 and a power of two chosen
+ * at lbm_init for the 16-bit kinds (so the largest |d_i| sits near 2^12).
+ * Collision arithmetic is FP32 for the FP32/FP16/BF16 kinds and FP64 for
+ * LBM_FP64 (which also stores deviations, in double). */
+typedef enum {
+    LBM_FP32 = 0,
+    LBM_FP16_DEV = 1,
+    LBM_BF16_DEV = 2,
+    LBM_FP64 = 3
+} lbm_precision;
+
+/* Which stream-collide kernel lbm_step launches. */
+typedef enum {
+    LBM_KERNEL_AUTO = 0,     /* fastest kernel valid for the lattice          */
+    LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx                   */
+    LBM_KERNEL_VECTOR = 2,   /* 16-byte vectors along x; nx % (16/size) == 0  */
+    LBM_KERNEL_STAGED = 3    /* bulk-copy (TMA engine) row staging in shared  */
+                             /* memory; same condition as VECTOR              */
+} lbm_kernel;
+
+typedef struct {
+    int nx;                  /* nodes along x (>= 1)                           */
+    int ny;                  /* nodes along y (>= 1; >= 2 with walls)          */
+} lbm_grid;
+
+typedef struct {
+    int x;                   /* LBM_BC_PERIODIC or LBM_BC_PERIODIC_GRADIENT    */
+    int y;                   /* LBM_BC_PERIODIC or LBM_BC_DIFFUSE_WALLS        */
+    double delta_e;          /* e_h - e_c of Eqs. 59-60 across one x period    */
+} lbm_boundary;
+
+/* Eq. 48 in lattice units: tau_X = Kn_X * length * sqrt(3/5), the relaxation
+ * time (in steps) of Knudsen number kn over a length of `length` cells. */
+double lbm_tau_from_kn(double kn, double length);
+
+/* Bytes of ONE population buffer (8 planes of ny*nx) for lbm_create_ex. */
+size_t lbm_population_bytes(lbm_grid grid, lbm_precision precision);
+
+/* Create a solver for a grid, relaxation times in lattice steps (tau_N and
+ * tau_R > 0, INFINITY allowed for either but not both; Section 2.1 and
+ * Eq. 49), boundaries and storage kind.  e_ref is the reference energy of the
+ * deviation storage (any finite value; the results do not depend on it up to
+ * rounding).  stream is a cudaStream_t (NULL = legacy default stream) on the
+ * current device, which the context remembers.
+ * Allocates two population buffers with cudaMalloc; freed by lbm_destroy.
+ * Errors: EINVAL (NULL out, grid too small, tau <= 1/2, tau_R <= 0, bad
+ * enum), EUNSUPPORTED (gradient on y, walls on x), ENOMEM, ECUDA. */
+lbm_status lbm_create(lbm_grid grid, double tau_N, double tau_R,
+                      lbm_boundary bc, lbm_precision precision, double e_ref,
+                      void *stream, lbm_ctx **out);
+
+/* As lbm_create, but the caller supplies the two population buffers
+ * (device pointers, 256-byte aligned, each at least
+ * lbm_population_bytes(grid, precision) bytes).  They stay owned by the
+ * caller and must outlive the context.  Scratch for moments and residuals is
+ * still allocated by the library on first use. */
+lbm_status lbm_create_ex(lbm_grid grid, double tau_N, double tau_R,
+                         lbm_boundary bc, lbm_precision precision,
+                         double e_ref, void *stream, void *buf_a, void *buf_b,
+                         size_t buf_bytes, lbm_ctx **out);
+
+/* Free everything the context allocated (never caller-owned buffers).
+ * Synchronises the context's stream first.  NULL is accepted. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Set step 0 to e_i = e_i^eq(e, q) (Eq. 15) from HOST fields e, qx, qy
+ * ([ny][nx] float64; qx or qy may be NULL for zero).  Resets the step count
+ * and the residual history.  Synchronous.  Errors: EINVAL (NULL ctx or e,
+ * non-finite input), ENOMEM, ECUDA. */
+lbm_status lbm_init(lbm_ctx *ctx, const double *e, const double *qx,
+                    const double *qy);
+
+/* As lbm_init with DEVICE fields (qx, qy may be NULL).  Synchronises once to
+ * read the largest deviation for the 16-bit scale. */
+lbm_status lbm_init_device(lbm_ctx *ctx, const double *e, const double *qx,
+                           const double *qy);
+
+/* Advance n >= 0 steps (Eq. 13 with the boundaries above).  Async; long runs
+ * replay a CUDA graph of a fixed chunk of steps.  Errors: EINVAL (n < 0,
+ * not initialised), ECUDA (launch failure). */
+lbm_status lbm_step(lbm_ctx *ctx, long n);
+
+/* Wait for the context's stream; ECUDA if a queued kernel failed. */
+lbm_status lbm_sync(lbm_ctx *ctx);
+
+/* e (Eq. 53) and q (Eq. 54) of the state at the current step, into HOST
+ * arrays [ny][nx] float64 (any of the three may be NULL).  Synchronous. */
+lbm_status lbm_moments(lbm_ctx *ctx, double *e, double *qx, double *qy);
+
+/* Same into DEVICE arrays of ny*nx float64 (any may be NULL).  Async. */
+lbm_status lbm_moments_device(lbm_ctx *ctx, double *e, double *qx,
+                              double *qy);
+
+/* The 8 populations e_i (not deviations) of the state at the current step,
+ * as float64 HOST array [8][ny][nx].  Synchronous. */
+lbm_status lbm_populations(lbm_ctx *ctx, double *f);
+
+/* Convergence residual and total energy, reduced in FP64 on the device.
+ *   r = ||(e, q)^n - (e, q)^m||_2 / ((n - m) ||(e - mean(e), q)^n||_2)
+ * where m is the step of the previous lbm_residual call since lbm_init
+ * (r = +INFINITY on the first call or when n == m), and
+ *   total_energy = sum over nodes of e (Eq. 53).
+ * Either output may be NULL.  Synchronous.  Errors: ENONFINITE when any
+ * e or q is NaN/Inf (outputs still written), ECUDA. */
+lbm_status lbm_residual(lbm_ctx *ctx, double *r, double *total_energy);
+
+/* Checkpoint: an opaque host blob of lbm_state_bytes(ctx) bytes holding the
+ * raw population buffers, the step count and the storage scale.
+ * lbm_set_state restores it into a context with the same grid, boundary
+ * kinds and storage kind; continuing gives bit-identical results. */
+size_t lbm_state_bytes(const lbm_ctx *ctx);
+lbm_status lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes);
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
+
+/* Steps taken since lbm_init (or restored by lbm_set_state). */
+long lbm_step_count(const lbm_ctx *ctx);
+
+/* Choose the stream-collide kernel (LBM_KERNEL_*).  EUNSUPPORTED when the
+ * kernel cannot run this lattice (e.g. VECTOR with a ragged nx). */
+lbm_status lbm_set_kernel(lbm_ctx *ctx, int kernel);
+
+/* The kernel lbm_step will launch (never LBM_KERNEL_AUTO). */
+int lbm_get_kernel(const lbm_ctx *ctx);
+
+/* Steps per captured CUDA graph chunk (even, >= 2), or 0 to launch every
+ * step directly.  Default 64. */
+lbm_status lbm_set_graph_chunk(lbm_ctx *ctx, int steps);
+
+/* Number of stream-collide kernel launches queued since lbm_init. */
+long long lbm_kernel_launches(const lbm_ctx *ctx);
+
+/* The storage scale s of the deviation (1 for FP32/FP64). */
+double lbm_storage_scale(const lbm_ctx *ctx);
+
+/* Text of the last failure on this context (or of the last failed
+ * lbm_create when ctx is NULL).  Never NULL; valid until the next call. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHONON_LBM_H */

@@ -1,0 +1,294 @@
+"""GB300 (sm_103a) phonon lattice Boltzmann solver - Python binding.
+
+The solver advances Guo & Wang's lattice Boltzmann scheme for the phonon
+Boltzmann equation under Callaway's dual relaxation model (arXiv
+2010.01847, Section 2) on a D2Q8 lattice.  Every step of the method runs in
+the CUDA kernels of ``libphonon_lbm.so`` behind the C-ABI declared in
+``include/phonon_lbm.h``; this module only marshals arguments through
+ctypes.  PyTorch supplies device memory (the two population buffers) and the
+CUDA stream.  There is no CPU fallback: without the compiled library or a
+CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphonon_lbm.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(7)
+PERIODIC, PERIODIC_GRADIENT, DIFFUSE_WALLS = 0, 1, 2
+FP32, FP16_DEV, BF16_DEV, FP64 = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_STAGED = 0, 1, 2, 3
+
+PRECISIONS = {"fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV, "fp64": FP64}
+KERNELS = {"auto": KERNEL_AUTO, "scalar": KERNEL_SCALAR, "vector": KERNEL_VECTOR,
+           "staged": KERNEL_STAGED}
+_ELEM = {FP32: 4, FP16_DEV: 2, BF16_DEV: 2, FP64: 8}
+
+# Every symbol include/phonon_lbm.h declares.
+EXPORTS = [
+    "lbm_tau_from_kn", "lbm_population_bytes", "lbm_create", "lbm_create_ex",
+    "lbm_destroy", "lbm_init", "lbm_init_device", "lbm_step", "lbm_sync",
+    "lbm_moments", "lbm_moments_device", "lbm_populations", "lbm_residual",
+    "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_step_count",
+    "lbm_set_kernel", "lbm_get_kernel", "lbm_set_graph_chunk",
+    "lbm_kernel_launches", "lbm_storage_scale", "lbm_last_error",
+]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[lbm status {status}] {message}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int)]
+
+
+class Boundary(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_int), ("y", ctypes.c_int), ("delta_e", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the compiled C-ABI library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; "
+            "g.build()'` (the CUDA path has no fallback)")
+    lib = ctypes.CDLL(path)
+    vp, dp, c_long, c_size = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), \
+        ctypes.c_long, ctypes.c_size_t
+    st = ctypes.c_int
+    sig = {
+        "lbm_tau_from_kn": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
+        "lbm_population_bytes": (c_size, [Grid, ctypes.c_int]),
+        "lbm_create": (st, [Grid, ctypes.c_double, ctypes.c_double, Boundary, ctypes.c_int,
+                            ctypes.c_double, vp, ctypes.POINTER(vp)]),
+        "lbm_create_ex": (st, [Grid, ctypes.c_double, ctypes.c_double, Boundary, ctypes.c_int,
+                               ctypes.c_double, vp, vp, vp, c_size, ctypes.POINTER(vp)]),
+        "lbm_destroy": (None, [vp]),
+        "lbm_init": (st, [vp, dp, dp, dp]),
+        "lbm_init_device": (st, [vp, vp, vp, vp]),
+        "lbm_step": (st, [vp, c_long]),
+        "lbm_sync": (st, [vp]),
+        "lbm_moments": (st, [vp, dp, dp, dp]),
+        "lbm_moments_device": (st, [vp, vp, vp, vp]),
+        "lbm_populations": (st, [vp, dp]),
+        "lbm_residual": (st, [vp, dp, dp]),
+        "lbm_state_bytes": (c_size, [vp]),
+        "lbm_get_state": (st, [vp, vp, c_size]),
+        "lbm_set_state": (st, [vp, vp, c_size]),
+        "lbm_step_count": (c_long, [vp]),
+        "lbm_set_kernel": (st, [vp, ctypes.c_int]),
+        "lbm_get_kernel": (ctypes.c_int, [vp]),
+        "lbm_set_graph_chunk": (st, [vp, ctypes.c_int]),
+        "lbm_kernel_launches": (ctypes.c_longlong, [vp]),
+        "lbm_storage_scale": (ctypes.c_double, [vp]),
+        "lbm_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def tau_from_kn(kn: float, length: float) -> float:
+    """Eq. 48 in lattice units: kn * length * sqrt(3/5)."""
+    return load_library().lbm_tau_from_kn(float(kn), float(length))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Lattice:
+    """One D2Q8 lattice on one GPU.
+
+    Parameters are in lattice units: ``tau_N``, ``tau_R`` are relaxation
+    times in steps (``math.inf`` allowed for one of them); ``bc_x`` is
+    PERIODIC or PERIODIC_GRADIENT (with ``delta_e`` = e_h - e_c of
+    Eqs. 59-60), ``bc_y`` is PERIODIC or DIFFUSE_WALLS (Eq. 58).
+    ``precision`` is one of "fp32", "fp16", "bf16", "fp64".
+    """
+
+    def __init__(self, nx, ny, tau_N, tau_R, bc_x=PERIODIC, bc_y=PERIODIC, delta_e=0.0,
+                 precision="fp32", e_ref=1.0, kernel="auto", device=None,
+                 torch_buffers=True, graph_chunk=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the phonon LBM runs only on the GPU")
+        self._lib = load_library()
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else device)
+        self.nx, self.ny = int(nx), int(ny)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._ctx = ctypes.c_void_p()
+        grid = Grid(self.nx, self.ny)
+        bc = Boundary(int(bc_x), int(bc_y), float(delta_e))
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+            sp = ctypes.c_void_p(self.stream.cuda_stream)
+            if torch_buffers:
+                nbytes = self._lib.lbm_population_bytes(grid, self.precision)
+                if nbytes == 0:
+                    raise LBMError(EINVAL, "invalid grid or precision")
+                self._bufs = [torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+                              for _ in range(2)]
+                st = self._lib.lbm_create_ex(grid, float(tau_N), float(tau_R), bc,
+                                             self.precision, float(e_ref), sp,
+                                             ctypes.c_void_p(self._bufs[0].data_ptr()),
+                                             ctypes.c_void_p(self._bufs[1].data_ptr()),
+                                             nbytes, ctypes.byref(self._ctx))
+            else:
+                self._bufs = []
+                st = self._lib.lbm_create(grid, float(tau_N), float(tau_R), bc, self.precision,
+                                          float(e_ref), sp, ctypes.byref(self._ctx))
+        if st != OK:
+            self._ctx = ctypes.c_void_p()
+            raise LBMError(st, self._lib.lbm_last_error(None).decode())
+        if kernel != "auto":
+            self.set_kernel(kernel)
+        if graph_chunk is not None:
+            self._check(self._lib.lbm_set_graph_chunk(self._ctx, int(graph_chunk)))
+
+    # -- plumbing -----------------------------------------------------------
+    def _check(self, st):
+        if st != OK:
+            raise LBMError(st, self._lib.lbm_last_error(self._ctx).decode())
+
+    def close(self):
+        if self._ctx:
+            self._lib.lbm_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+        self._bufs = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._ctx
+
+    # -- the solver ---------------------------------------------------------
+    def init(self, e, qx=None, qy=None):
+        """Step 0 = equilibrium of Eq. 15 from (e, q).  Host numpy arrays
+        (or scalars) of shape [ny, nx], or CUDA float64 tensors."""
+        torch = self.torch
+        if isinstance(e, torch.Tensor) and e.is_cuda:
+            def dev(a):
+                if a is None:
+                    return None
+                a = a.to(device=self.device, dtype=torch.float64).contiguous()
+                assert a.numel() == self.nx * self.ny
+                return a
+            e, qx, qy = dev(e), dev(qx), dev(qy)
+            self._keep = (e, qx, qy)
+            ptr = lambda a: ctypes.c_void_p(a.data_ptr()) if a is not None else None
+            self._check(self._lib.lbm_init_device(self._ctx, ptr(e), ptr(qx), ptr(qy)))
+            return
+        shape = (self.ny, self.nx)
+        host = lambda a: None if a is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(a, dtype=np.float64), shape))
+        e, qx, qy = host(e), host(qx), host(qy)
+        p = lambda a: _dptr(a) if a is not None else None
+        self._check(self._lib.lbm_init(self._ctx, p(e), p(qx), p(qy)))
+
+    def step(self, n: int = 1):
+        self._check(self._lib.lbm_step(self._ctx, int(n)))
+
+    def sync(self):
+        self._check(self._lib.lbm_sync(self._ctx))
+
+    def moments(self):
+        """(e, qx, qy) of the current state as numpy [ny, nx] float64."""
+        e = np.empty((self.ny, self.nx))
+        qx = np.empty_like(e)
+        qy = np.empty_like(e)
+        self._check(self._lib.lbm_moments(self._ctx, _dptr(e), _dptr(qx), _dptr(qy)))
+        return e, qx, qy
+
+    def moments_device(self, out=None):
+        """(e, qx, qy) as CUDA float64 tensors [ny, nx] (async)."""
+        torch = self.torch
+        if out is None:
+            out = [torch.empty((self.ny, self.nx), dtype=torch.float64, device=self.device)
+                   for _ in range(3)]
+        ptrs = [ctypes.c_void_p(t.data_ptr()) for t in out]
+        self._check(self._lib.lbm_moments_device(self._ctx, *ptrs))
+        return out
+
+    def populations(self):
+        """Raw populations e_i of the current state, numpy [8, ny, nx]."""
+        f = np.empty((8, self.ny, self.nx))
+        self._check(self._lib.lbm_populations(self._ctx, _dptr(f)))
+        return f
+
+    def residual(self):
+        """(r, total energy): FP64 device reduction (see lbm_residual)."""
+        r, en = ctypes.c_double(), ctypes.c_double()
+        st = self._lib.lbm_residual(self._ctx, ctypes.byref(r), ctypes.byref(en))
+        self._check(st)
+        return r.value, en.value
+
+    def get_state(self) -> bytes:
+        n = self._lib.lbm_state_bytes(self._ctx)
+        buf = ctypes.create_string_buffer(n)
+        self._check(self._lib.lbm_get_state(self._ctx, buf, n))
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._check(self._lib.lbm_set_state(self._ctx, buf, len(blob)))
+
+    @property
+    def step_count(self) -> int:
+        return self._lib.lbm_step_count(self._ctx)
+
+    @property
+    def kernel_launches(self) -> int:
+        return self._lib.lbm_kernel_launches(self._ctx)
+
+    @property
+    def storage_scale(self) -> float:
+        return self._lib.lbm_storage_scale(self._ctx)
+
+    def set_kernel(self, kernel):
+        k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        self._check(self._lib.lbm_set_kernel(self._ctx, k))
+
+    @property
+    def kernel(self) -> str:
+        k = self._lib.lbm_get_kernel(self._ctx)
+        return {v: n for n, v in KERNELS.items()}[k]
+
+    def set_graph_chunk(self, steps: int):
+        self._check(self._lib.lbm_set_graph_chunk(self._ctx, int(steps)))
+
+    @property
+    def bytes_per_site_update(self) -> int:
+        """Algorithmic bytes per site update: 8 populations read + 8 written."""
+        return 16 * _ELEM[self.precision]

@@ -1,0 +1,632 @@
+// C-ABI of the phonon lattice Boltzmann solver (declared in phonon_lbm.h):
+// argument checking, device memory, kernel selection, CUDA-graph step
+// chunks, read-outs and checkpoints.  All arithmetic of the scheme runs in
+// the kernels of stream_collide.cu, staged.cu and readout.cu.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/phonon_lbm.h"
+#include "lbm_kernels.h"
+
+using namespace plbm;
+
+struct lbm_ctx {
+    int device = 0;
+    int nx = 0, ny = 0;
+    long long plane = 0;
+    int bc_x = 0, bc_y = 0;
+    double delta_e = 0.0;
+    double tau_N = 0.0, tau_R = 0.0, tau = 0.0, tau_r = 0.0, kappa = 1.0, sigma = 0.0;
+    int precision = 0;
+    double e_ref = 1.0;
+    double scale = 1.0;
+    cudaStream_t stream = nullptr;
+    void *buf[2] = {nullptr, nullptr};
+    bool owns_buf = false;
+    size_t buf_bytes = 0;
+    int cur = 0;           // buffer with the post-collision populations of step n
+    long n = 0;            // steps since lbm_init
+    bool initialised = false;
+    int kernel = KERNEL_SCALAR;
+    int graph_chunk = 64;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    double *prev = nullptr;     // residual history, 3 planes of doubles
+    bool have_prev = false;
+    long prev_step = 0;
+    double *fields = nullptr;   // 3 planes of doubles: init staging / read-outs
+    double *partials = nullptr;
+    double *sums = nullptr;
+    unsigned long long *maxbits = nullptr;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr uint64_t STATE_MAGIC = 0x314d424c4e4f4850ULL;   // "PHONLBM1"
+
+struct StateHeader {
+    uint64_t magic;
+    int32_t version, nx, ny, precision, bc_x, bc_y, cur, pad;
+    int64_t n;
+    double scale;
+    uint64_t buf_bytes;
+};
+
+size_t elem_size(int precision) {
+    switch (precision) {
+        case PREC_FP32: return 4;
+        case PREC_FP64: return 8;
+        default: return 2;
+    }
+}
+
+lbm_status fail(lbm_ctx *ctx, lbm_status s, const std::string &msg) {
+    if (ctx)
+        ctx->err = msg;
+    else
+        g_create_error = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx *ctx, cudaError_t e, const char *where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                      cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, LBM_ENOMEM, msg);
+    return fail(ctx, LBM_ECUDA, msg);
+}
+
+#define CK(ctx, call)                                        \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int old = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&old) == cudaSuccess && old != dev) cudaSetDevice(dev);
+        else old = -1;
+    }
+    ~DeviceGuard() {
+        if (old >= 0) cudaSetDevice(old);
+    }
+};
+
+template <typename C>
+Coef<C> make_coef(const lbm_ctx *c) {
+    // Eqs. 13, 15-18, 54 and 58 as the coefficients of lbm_device.cuh.
+    Coef<C> k;
+    k.omega = (C)(1.0 / c->tau);
+    k.sigma = (C)c->sigma;
+    k.lambda = (C)(std::isinf(c->tau_r) ? 0.0 : 1.0 / (2.0 * c->tau_r + 1.0));
+    k.w_axis = (C)(2.0 / 9.0);
+    k.w_diag = (C)0.25 - k.w_axis;                  // exact: 4 w_axis + 4 w_diag = 1
+    k.h_axis = (C)(1.0 / 3.0);
+    k.h_diag = ((C)1 - (C)2 * k.h_axis) / (C)4;     // exact: 2 h_axis + 4 h_diag = 1
+    k.u_axis = (C)0.8;
+    k.u_diag = ((C)1 - k.u_axis) / (C)2;            // exact: u_axis + 2 u_diag = 1
+    k.jump_axis = (C)(c->scale * (2.0 / 9.0) * c->delta_e);
+    k.jump_diag = (C)(c->scale * (1.0 / 36.0) * c->delta_e);
+    return k;
+}
+
+Readout make_readout(const lbm_ctx *c) {
+    Readout r;
+    r.nx = c->nx;
+    r.ny = c->ny;
+    r.bc_x = c->bc_x;
+    r.bc_y = c->bc_y;
+    r.pulled = c->n > 0;
+    r.e_ref = c->e_ref;
+    r.inv_scale = 1.0 / c->scale;
+    r.kappa = c->kappa;
+    return r;
+}
+
+// Calls F<T>(ctx...) for the context's storage type.
+template <template <typename> class F, typename... A>
+cudaError_t dispatch(const lbm_ctx *c, A... a) {
+    switch (c->precision) {
+        case PREC_FP32: return F<float>::run(c, a...);
+        case PREC_FP64: return F<double>::run(c, a...);
+        case PREC_FP16: return F<__half>::run(c, a...);
+        default: return F<__nv_bfloat16>::run(c, a...);
+    }
+}
+
+template <typename T> struct StepOp {
+    static cudaError_t run(const lbm_ctx *c, int src, cudaStream_t s) {
+        using C = typename Store<T>::C;
+        return launch_step<T>(c->kernel, (const T *)c->buf[src], (T *)c->buf[1 - src], c->nx,
+                              c->ny, c->bc_x, c->bc_y, make_coef<C>(c), s);
+    }
+};
+template <typename T> struct MomentsOp {
+    static cudaError_t run(const lbm_ctx *c, double *e, double *qx, double *qy) {
+        using C = typename Store<T>::C;
+        return launch_moments<T>((const T *)c->buf[1 - c->cur], make_readout(c), make_coef<C>(c),
+                                 e, qx, qy, c->stream);
+    }
+};
+template <typename T> struct PopulationsOp {
+    static cudaError_t run(const lbm_ctx *c, double *f) {
+        using C = typename Store<T>::C;
+        return launch_populations<T>((const T *)c->buf[1 - c->cur], make_readout(c),
+                                     make_coef<C>(c), f, c->stream);
+    }
+};
+template <typename T> struct ResidualOp {
+    static cudaError_t run(const lbm_ctx *c, int dummy) {
+        (void)dummy;
+        using C = typename Store<T>::C;
+        return launch_residual<T>((const T *)c->buf[1 - c->cur], make_readout(c),
+                                  make_coef<C>(c), c->prev, c->have_prev, c->partials, c->sums,
+                                  c->stream);
+    }
+};
+template <typename T> struct InitOp {
+    static cudaError_t run(const lbm_ctx *c, const double *e, const double *qx,
+                           const double *qy) {
+        using C = typename Store<T>::C;
+        // step 0 state -> buffer 1, its collision -> buffer 0 (cur = 0)
+        return launch_init<T>(e, qx, qy, c->nx, c->ny, c->e_ref, c->scale, make_coef<C>(c),
+                              (T *)c->buf[1], (T *)c->buf[0], c->stream);
+    }
+};
+
+void drop_graphs(lbm_ctx *c) {
+    for (int i = 0; i < 2; ++i) {
+        if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+        c->graph[i] = nullptr;
+    }
+}
+
+lbm_status ensure_scratch(lbm_ctx *c, bool need_prev) {
+    if (!c->fields) CK(c, cudaMalloc(&c->fields, sizeof(double) * 3 * (size_t)c->plane));
+    if (!c->partials) CK(c, cudaMalloc(&c->partials, sizeof(double) * 5 * RESIDUAL_BLOCKS));
+    if (!c->sums) CK(c, cudaMalloc(&c->sums, sizeof(double) * 5));
+    if (!c->maxbits) CK(c, cudaMalloc(&c->maxbits, sizeof(unsigned long long)));
+    if (need_prev && !c->prev)
+        CK(c, cudaMalloc(&c->prev, sizeof(double) * 3 * (size_t)c->plane));
+    return LBM_OK;
+}
+
+int resolve_kernel(const lbm_ctx *c, int requested) {
+    const bool vec_ok = c->nx % vector_width(c->precision) == 0;
+    if (requested == KERNEL_AUTO) {
+        if (staged_supported(c->precision, c->nx, c->ny)) return KERNEL_STAGED;
+        return vec_ok ? KERNEL_VECTOR : KERNEL_SCALAR;
+    }
+    if (requested == KERNEL_VECTOR && !vec_ok) return -1;
+    if (requested == KERNEL_STAGED && !staged_supported(c->precision, c->nx, c->ny)) return -1;
+    return requested;
+}
+
+lbm_status create_common(lbm_grid g, double tau_N, double tau_R, lbm_boundary bc,
+                         lbm_precision precision, double e_ref, void *stream, void *buf_a,
+                         void *buf_b, size_t buf_bytes, lbm_ctx **out) {
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (g.nx < 1 || g.ny < 1) return fail(nullptr, LBM_EINVAL, "grid must be at least 1x1");
+    if ((long long)g.nx * g.ny > (1LL << 40))
+        return fail(nullptr, LBM_EINVAL, "grid too large");
+    if (bc.x == LBM_BC_DIFFUSE_WALLS)
+        return fail(nullptr, LBM_EUNSUPPORTED, "diffuse walls are supported on y only");
+    if (bc.y == LBM_BC_PERIODIC_GRADIENT)
+        return fail(nullptr, LBM_EUNSUPPORTED,
+                    "the periodic temperature gradient is supported on x only");
+    if ((bc.x != LBM_BC_PERIODIC && bc.x != LBM_BC_PERIODIC_GRADIENT) ||
+        (bc.y != LBM_BC_PERIODIC && bc.y != LBM_BC_DIFFUSE_WALLS))
+        return fail(nullptr, LBM_EINVAL, "unknown boundary kind");
+    if (bc.y == LBM_BC_DIFFUSE_WALLS && g.ny < 2)
+        return fail(nullptr, LBM_EINVAL, "diffuse walls need ny >= 2");
+    if (!std::isfinite(bc.delta_e)) return fail(nullptr, LBM_EINVAL, "delta_e is not finite");
+    if (!std::isfinite(e_ref)) return fail(nullptr, LBM_EINVAL, "e_ref is not finite");
+    if (std::isnan(tau_N) || std::isnan(tau_R) || !(tau_N > 0.0) || !(tau_R > 0.0))
+        return fail(nullptr, LBM_EINVAL, "tau_N and tau_R must be > 0");
+    if (std::isinf(tau_N) && std::isinf(tau_R))
+        return fail(nullptr, LBM_EINVAL, "tau_N and tau_R cannot both be infinite");
+    if (precision < LBM_FP32 || precision > LBM_FP64)
+        return fail(nullptr, LBM_EINVAL, "unknown precision");
+
+    lbm_ctx *c = new lbm_ctx();
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(nullptr, e, "cudaGetDevice");
+    }
+    c->nx = g.nx;
+    c->ny = g.ny;
+    c->plane = (long long)g.nx * g.ny;
+    c->bc_x = bc.x;
+    c->bc_y = bc.y;
+    c->delta_e = bc.delta_e;
+    c->tau_N = tau_N;
+    c->tau_R = tau_R;
+    // Section 2.1: 1/tau_C = 1/tau_N + 1/tau_R; Eq. 49: tau = tau_C + 1/2;
+    // Section 2.4: tau_r = tau_R; Eq. 54: kappa; Eq. 16: sigma.
+    const double inv_c = (std::isinf(tau_N) ? 0.0 : 1.0 / tau_N) +
+                         (std::isinf(tau_R) ? 0.0 : 1.0 / tau_R);
+    c->tau = 1.0 / inv_c + 0.5;
+    c->tau_r = tau_R;
+    c->kappa = std::isinf(tau_R) ? 1.0 : 2.0 * tau_R / (2.0 * tau_R + 1.0);
+    c->sigma = std::isinf(tau_R) ? 0.0 : (1.0 - 1.0 / (2.0 * c->tau)) / tau_R;
+    c->precision = precision;
+    c->e_ref = e_ref;
+    c->stream = (cudaStream_t)stream;
+    c->buf_bytes = lbm_population_bytes(g, precision);
+    c->kernel = resolve_kernel(c, KERNEL_AUTO);
+
+    if (buf_a || buf_b) {
+        if (!buf_a || !buf_b || buf_a == buf_b) {
+            delete c;
+            return fail(nullptr, LBM_EINVAL, "need two distinct caller buffers");
+        }
+        if (buf_bytes < c->buf_bytes) {
+            delete c;
+            return fail(nullptr, LBM_EINVAL, "caller buffers are too small");
+        }
+        if (((uintptr_t)buf_a | (uintptr_t)buf_b) & 255u) {
+            delete c;
+            return fail(nullptr, LBM_EINVAL, "caller buffers must be 256-byte aligned");
+        }
+        c->buf[0] = buf_a;
+        c->buf[1] = buf_b;
+        c->owns_buf = false;
+    } else {
+        for (int i = 0; i < 2; ++i) {
+            e = cudaMalloc(&c->buf[i], c->buf_bytes);
+            if (e != cudaSuccess) {
+                lbm_status s = cuda_fail(nullptr, e, "cudaMalloc(population buffer)");
+                if (c->buf[0]) cudaFree(c->buf[0]);
+                delete c;
+                return s;
+            }
+        }
+        c->owns_buf = true;
+    }
+    e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        lbm_status s = cuda_fail(nullptr, e, "cudaStreamCreateWithFlags");
+        lbm_destroy(c);
+        return s;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status init_from_device(lbm_ctx *c, const double *e, const double *qx, const double *qy) {
+    if (lbm_status s = ensure_scratch(c, false)) return s;
+    CK(c, cudaMemsetAsync(c->maxbits, 0, sizeof(unsigned long long), c->stream));
+    CK(c, launch_max_deviation(e, qx, qy, c->plane, c->e_ref, c->maxbits, c->stream));
+    unsigned long long bits = 0;
+    CK(c, cudaMemcpyAsync(&bits, c->maxbits, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    double amax;
+    std::memcpy(&amax, &bits, sizeof(amax));
+    if (!std::isfinite(amax)) return fail(c, LBM_EINVAL, "initial fields are not finite");
+    c->scale = 1.0;
+    if (c->precision == PREC_FP16 || c->precision == PREC_BF16) {
+        // largest |d_i| ~ 2^12 after scaling: room for 16x growth below the
+        // FP16 maximum, far above its smallest normal number
+        const double a = std::fmax(amax, (2.0 / 9.0) * std::fabs(c->delta_e));
+        if (a > 0.0) {
+            int ex;
+            std::frexp(a, &ex);        // a < 2^ex
+            int p = 12 - ex;
+            p = p > 100 ? 100 : (p < -100 ? -100 : p);
+            c->scale = std::ldexp(1.0, p);
+        }
+    }
+    drop_graphs(c);
+    CK(c, dispatch<InitOp>(c, e, qx, qy));
+    c->cur = 0;
+    c->n = 0;
+    c->have_prev = false;
+    c->prev_step = 0;
+    c->launches = 0;
+    c->initialised = true;
+    return LBM_OK;
+}
+
+lbm_status build_graph(lbm_ctx *c, int start) {
+    CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int src = start;
+    cudaError_t le = cudaSuccess;
+    for (int s = 0; s < c->graph_chunk && le == cudaSuccess; ++s) {
+        le = dispatch<StepOp>(c, src, c->cap_stream);
+        src = 1 - src;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, le, "capture of stream-collide launches");
+    }
+    if (ee != cudaSuccess) return cuda_fail(c, ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&c->graph[start], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        c->graph[start] = nullptr;
+        return cuda_fail(c, ie, "cudaGraphInstantiate");
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+double lbm_tau_from_kn(double kn, double length) { return kn * length * std::sqrt(3.0 / 5.0); }
+
+size_t lbm_population_bytes(lbm_grid grid, lbm_precision precision) {
+    if (grid.nx < 1 || grid.ny < 1 || precision < LBM_FP32 || precision > LBM_FP64) return 0;
+    return (size_t)8 * (size_t)grid.nx * (size_t)grid.ny * elem_size(precision);
+}
+
+lbm_status lbm_create(lbm_grid grid, double tau_N, double tau_R, lbm_boundary bc,
+                      lbm_precision precision, double e_ref, void *stream, lbm_ctx **out) {
+    return create_common(grid, tau_N, tau_R, bc, precision, e_ref, stream, nullptr, nullptr, 0,
+                         out);
+}
+
+lbm_status lbm_create_ex(lbm_grid grid, double tau_N, double tau_R, lbm_boundary bc,
+                         lbm_precision precision, double e_ref, void *stream, void *buf_a,
+                         void *buf_b, size_t buf_bytes, lbm_ctx **out) {
+    if (!buf_a || !buf_b) return fail(nullptr, LBM_EINVAL, "caller buffers are NULL");
+    return create_common(grid, tau_N, tau_R, bc, precision, e_ref, stream, buf_a, buf_b,
+                         buf_bytes, out);
+}
+
+void lbm_destroy(lbm_ctx *c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->owns_buf) {
+        cudaFree(c->buf[0]);
+        cudaFree(c->buf[1]);
+    }
+    cudaFree(c->prev);
+    cudaFree(c->fields);
+    cudaFree(c->partials);
+    cudaFree(c->sums);
+    cudaFree(c->maxbits);
+    delete c;
+}
+
+lbm_status lbm_init(lbm_ctx *c, const double *e, const double *qx, const double *qy) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!e) return fail(c, LBM_EINVAL, "e is NULL");
+    DeviceGuard g(c->device);
+    const long long n = c->plane;
+    const double *src[3] = {e, qx, qy};
+    // non-finite inputs are caught on the device by the scale pass
+    if (lbm_status s = ensure_scratch(c, false)) return s;
+    for (int f = 0; f < 3; ++f)
+        if (src[f])
+            CK(c, cudaMemcpyAsync(c->fields + f * n, src[f], sizeof(double) * n,
+                                  cudaMemcpyHostToDevice, c->stream));
+    return init_from_device(c, c->fields, qx ? c->fields + n : nullptr,
+                            qy ? c->fields + 2 * n : nullptr);
+}
+
+lbm_status lbm_init_device(lbm_ctx *c, const double *e, const double *qx, const double *qy) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!e) return fail(c, LBM_EINVAL, "e is NULL");
+    DeviceGuard g(c->device);
+    return init_from_device(c, e, qx, qy);
+}
+
+lbm_status lbm_step(lbm_ctx *c, long n) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+    if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    DeviceGuard g(c->device);
+    long left = n;
+    if (c->graph_chunk > 0 && left >= c->graph_chunk) {
+        if (!c->graph[c->cur])
+            if (lbm_status s = build_graph(c, c->cur)) return s;
+        while (left >= c->graph_chunk) {
+            CK(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+            left -= c->graph_chunk;
+            c->n += c->graph_chunk;
+            c->launches += c->graph_chunk;
+        }
+    }
+    for (; left > 0; --left) {
+        CK(c, dispatch<StepOp>(c, c->cur, c->stream));
+        c->cur = 1 - c->cur;
+        c->n += 1;
+        c->launches += 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx *c) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    DeviceGuard g(c->device);
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_moments_device(lbm_ctx *c, double *e, double *qx, double *qy) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    DeviceGuard g(c->device);
+    if (!e && !qx && !qy) return LBM_OK;
+    CK(c, dispatch<MomentsOp>(c, e, qx, qy));
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx *c, double *e, double *qx, double *qy) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    DeviceGuard g(c->device);
+    if (!e && !qx && !qy) return LBM_OK;
+    if (lbm_status s = ensure_scratch(c, false)) return s;
+    const long long n = c->plane;
+    double *d[3] = {c->fields, c->fields + n, c->fields + 2 * n};
+    CK(c, dispatch<MomentsOp>(c, d[0], d[1], d[2]));
+    double *h[3] = {e, qx, qy};
+    for (int f = 0; f < 3; ++f)
+        if (h[f])
+            CK(c, cudaMemcpyAsync(h[f], d[f], sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                  c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_populations(lbm_ctx *c, double *f) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!f) return fail(c, LBM_EINVAL, "f is NULL");
+    if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    DeviceGuard g(c->device);
+    double *dev = nullptr;
+    CK(c, cudaMallocAsync((void **)&dev, sizeof(double) * 8 * (size_t)c->plane, c->stream));
+    cudaError_t e = dispatch<PopulationsOp>(c, dev);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f, dev, sizeof(double) * 8 * (size_t)c->plane,
+                            cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(dev, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_populations");
+    return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_ctx *c, double *r, double *total_energy) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    DeviceGuard g(c->device);
+    if (lbm_status s = ensure_scratch(c, true)) return s;
+    CK(c, dispatch<ResidualOp>(c, 0));
+    double sums[5];
+    CK(c, cudaMemcpyAsync(sums, c->sums, sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const double n = (double)c->plane;
+    const double mean = sums[0] / n;
+    const double var_e = std::fmax(sums[1] - n * mean * mean, 0.0);
+    const double denom = std::sqrt(var_e + sums[2]);
+    const long k = c->n - c->prev_step;
+    double res = INFINITY;
+    if (c->have_prev && k > 0) {
+        const double num = std::sqrt(sums[3]);
+        res = denom > 0.0 ? num / ((double)k * denom) : (num == 0.0 ? 0.0 : INFINITY);
+    }
+    c->have_prev = true;
+    c->prev_step = c->n;
+    if (r) *r = res;
+    if (total_energy) *total_energy = n * c->e_ref + sums[0];
+    if (sums[4] > 0.0) return fail(c, LBM_ENONFINITE, "state holds NaN or Inf");
+    return LBM_OK;
+}
+
+size_t lbm_state_bytes(const lbm_ctx *c) {
+    if (!c) return 0;
+    return sizeof(StateHeader) + 2 * c->buf_bytes;
+}
+
+lbm_status lbm_get_state(lbm_ctx *c, void *host, size_t bytes) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!host) return fail(c, LBM_EINVAL, "host is NULL");
+    if (bytes < lbm_state_bytes(c)) return fail(c, LBM_EINVAL, "state buffer too small");
+    if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    DeviceGuard g(c->device);
+    StateHeader h{};
+    h.magic = STATE_MAGIC;
+    h.version = 1;
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.precision = c->precision;
+    h.bc_x = c->bc_x;
+    h.bc_y = c->bc_y;
+    h.cur = c->cur;
+    h.n = c->n;
+    h.scale = c->scale;
+    h.buf_bytes = c->buf_bytes;
+    char *p = (char *)host;
+    std::memcpy(p, &h, sizeof(h));
+    for (int i = 0; i < 2; ++i)
+        CK(c, cudaMemcpyAsync(p + sizeof(h) + i * c->buf_bytes, c->buf[i], c->buf_bytes,
+                              cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx *c, const void *host, size_t bytes) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!host) return fail(c, LBM_EINVAL, "host is NULL");
+    if (bytes < sizeof(StateHeader)) return fail(c, LBM_EINVAL, "state blob too small");
+    StateHeader h;
+    std::memcpy(&h, host, sizeof(h));
+    if (h.magic != STATE_MAGIC || h.version != 1)
+        return fail(c, LBM_EINVAL, "not a phonon LBM state blob");
+    if (h.nx != c->nx || h.ny != c->ny || h.precision != c->precision || h.bc_x != c->bc_x ||
+        h.bc_y != c->bc_y || h.buf_bytes != c->buf_bytes || (h.cur != 0 && h.cur != 1) ||
+        h.n < 0 || !(h.scale > 0.0))
+        return fail(c, LBM_EINVAL, "state blob does not match this context");
+    if (bytes < lbm_state_bytes(c)) return fail(c, LBM_EINVAL, "state blob truncated");
+    DeviceGuard g(c->device);
+    const char *p = (const char *)host;
+    for (int i = 0; i < 2; ++i)
+        CK(c, cudaMemcpyAsync(c->buf[i], p + sizeof(h) + i * c->buf_bytes, c->buf_bytes,
+                              cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+    c->cur = h.cur;
+    c->n = h.n;
+    c->scale = h.scale;
+    c->have_prev = false;
+    c->prev_step = c->n;
+    c->initialised = true;
+    return LBM_OK;
+}
+
+long lbm_step_count(const lbm_ctx *c) { return c ? c->n : -1; }
+
+lbm_status lbm_set_kernel(lbm_ctx *c, int kernel) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (kernel < KERNEL_AUTO || kernel > KERNEL_STAGED)
+        return fail(c, LBM_EINVAL, "unknown kernel");
+    const int k = resolve_kernel(c, kernel);
+    if (k < 0) return fail(c, LBM_EUNSUPPORTED, "kernel cannot run this lattice");
+    if (k != c->kernel) {
+        DeviceGuard g(c->device);
+        drop_graphs(c);
+        c->kernel = k;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_kernel(const lbm_ctx *c) { return c ? c->kernel : -1; }
+
+lbm_status lbm_set_graph_chunk(lbm_ctx *c, int steps) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (steps < 0 || steps == 1 || (steps & 1))
+        return fail(c, LBM_EINVAL, "graph chunk must be 0 or an even number >= 2");
+    DeviceGuard g(c->device);
+    drop_graphs(c);
+    c->graph_chunk = steps;
+    return LBM_OK;
+}
+
+long long lbm_kernel_launches(const lbm_ctx *c) { return c ? c->launches : -1; }
+
+double lbm_storage_scale(const lbm_ctx *c) { return c ? c->scale : 0.0; }
+
+const char *lbm_last_error(const lbm_ctx *c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+}  // extern "C"

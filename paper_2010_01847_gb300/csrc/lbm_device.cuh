@@ -1,0 +1,149 @@
+// Device-side building blocks of the D2Q8 phonon lattice Boltzmann step
+// (Guo & Wang, Section 2.2): storage traits, the collision on deviations,
+// and the boundary rules applied to pulled populations.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace plbm {
+
+// Eq. 14 in the order Eqs. 59-60 imply; index i = the paper's direction i+1.
+//   0:(1,0) 1:(0,1) 2:(-1,0) 3:(0,-1) 4:(1,1) 5:(-1,1) 6:(-1,-1) 7:(1,-1)
+__host__ __device__ constexpr int cx_of(int i) {
+    return (i == 0 || i == 4 || i == 7) ? 1 : (i == 2 || i == 5 || i == 6) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy_of(int i) {
+    return (i == 1 || i == 4 || i == 5) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+
+enum { BC_PERIODIC = 0, BC_GRADIENT = 1, BC_WALLS = 2 };
+
+// Coefficients of the collision, computed on the host in FP64 and rounded
+// once to the compute type C.  On deviations d_i (scaled by s), with
+//   rho = sum d_i, m = sum c_i d_i, q = m - lambda m  (Eq. 54, kappa = 1 - lambda),
+//   t_i = h_i (c_i . q)                      ((5/3) a_i c_i.q of Eqs. 15-16),
+//   eq_i = w_i rho + t_i                     (Eq. 15 on deviations),
+// the post-collision deviation is (Eq. 13 right-hand side with Eq. 16)
+//   d_i* = d_i - omega (d_i - eq_i) - sigma t_i,
+// omega = 1/tau, sigma = (1 - 1/(2 tau)) / tau_r.
+// The rounded coefficients keep the sums the scheme conserves exact in the
+// rounded values: 4 w_axis + 4 w_diag = 1, 2 h_axis + 4 h_diag = 1 and
+// u_axis + 2 u_diag = 1 hold exactly (w_diag = 1/4 - w_axis and the other
+// two are exact in binary floating point), and 1 - kappa is carried as
+// lambda rather than recovered from a rounded kappa.  Otherwise a rounded
+// coefficient would bias every step the same way and the bias would grow
+// linearly with the step count.
+template <typename C>
+struct Coef {
+    C omega, sigma, lambda;
+    C w_axis, w_diag;         // Eq. 17
+    C h_axis, h_diag;         // (5/3) a_i, Eq. 18
+    C u_axis, u_diag;         // Eq. 58: w_i / (5/18) = 4/5 and 1/10
+    C jump_axis, jump_diag;   // s w_i delta_e, Eqs. 59-60
+};
+
+// Storage traits: how a population plane element is stored and converted.
+template <typename T> struct Store;
+template <> struct Store<float> {
+    using C = float;
+    __device__ static C load(float v) { return v; }
+    __device__ static float put(C v) { return v; }
+};
+template <> struct Store<double> {
+    using C = double;
+    __device__ static C load(double v) { return v; }
+    __device__ static double put(C v) { return v; }
+};
+template <> struct Store<__half> {
+    using C = float;
+    __device__ static C load(__half v) { return __half2float(v); }
+    __device__ static __half put(C v) { return __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    using C = float;
+    __device__ static C load(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __nv_bfloat16 put(C v) { return __float2bfloat16_rn(v); }
+};
+
+// Collision of one node, in place on the 8 pulled deviations.
+template <typename C>
+__device__ __forceinline__ void collide(C (&d)[8], const Coef<C> &k) {
+    const C rho = ((d[0] + d[2]) + (d[1] + d[3])) + ((d[4] + d[6]) + (d[5] + d[7]));
+    const C mx = (d[0] - d[2]) + (d[4] - d[6]) + (d[7] - d[5]);
+    const C my = (d[1] - d[3]) + (d[4] - d[6]) + (d[5] - d[7]);
+    const C qx = mx - k.lambda * mx;
+    const C qy = my - k.lambda * my;
+    const C wa = k.w_axis * rho;
+    const C wd = k.w_diag * rho;
+    // t_i for i = 0..7: c_i.q = qx, qy, -qx, -qy, qx+qy, qy-qx, -qx-qy, qx-qy
+    const C ta = k.h_axis * qx;
+    const C tb = k.h_axis * qy;
+    const C tp = k.h_diag * (qx + qy);
+    const C tm = k.h_diag * (qx - qy);
+    const C t[8] = {ta, tb, -ta, -tb, tp, -tm, -tp, tm};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const C eq = (i < 4 ? wa : wd) + t[i];
+        d[i] = d[i] - k.omega * (d[i] - eq) - k.sigma * t[i];
+    }
+}
+
+// Eq. 58 on a wall node whose pulled incident populations are in d.
+// Bottom wall (y = 0, outward normal (0,-1)): unknown 1,4,5 from incident
+// 3,6,7; top wall (y = ny-1): unknown 3,6,7 from incident 1,4,5.  The sum of
+// w over the unknowns is 5/18, so w_i/(5/18) is 4/5 (axis) or 1/10 (diag).
+template <typename C>
+__device__ __forceinline__ void wall_bottom(C (&d)[8], const Coef<C> &k) {
+    const C s = d[3] + d[6] + d[7];
+    d[1] = k.u_axis * s;
+    d[4] = k.u_diag * s;
+    d[5] = k.u_diag * s;
+}
+template <typename C>
+__device__ __forceinline__ void wall_top(C (&d)[8], const Coef<C> &k) {
+    const C s = d[1] + d[4] + d[5];
+    d[3] = k.u_axis * s;
+    d[6] = k.u_diag * s;
+    d[7] = k.u_diag * s;
+}
+
+// Generic pull of the 8 populations arriving at node (x, y) at the next
+// step from the post-collision planes `src` (one node, any nx).  Applies the
+// seam jump and the walls.  Used by the scalar step kernel and by every
+// read-out kernel.
+template <typename T>
+__device__ __forceinline__ void pull_node(const T *__restrict__ src, long long plane,
+                                          int nx, int ny, int x, int y, int bc_x,
+                                          int bc_y, const Coef<typename Store<T>::C> &k,
+                                          typename Store<T>::C (&d)[8]) {
+    using C = typename Store<T>::C;
+    const bool walls = bc_y == BC_WALLS;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i);
+        int sy = y - cy;
+        if (walls && (sy < 0 || sy >= ny)) {
+            d[i] = C(0);          // unknown: filled by Eq. 58 below
+            continue;
+        }
+        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+        int sx = x - cx;
+        C jump = C(0);
+        if (sx < 0) {             // crossed the seam moving right (Eq. 59)
+            sx += nx;
+            if (bc_x == BC_GRADIENT) jump = (i < 4) ? k.jump_axis : k.jump_diag;
+        } else if (sx >= nx) {    // crossed the seam moving left (Eq. 60)
+            sx -= nx;
+            if (bc_x == BC_GRADIENT) jump = -((i < 4) ? k.jump_axis : k.jump_diag);
+        }
+        d[i] = Store<T>::load(src[(long long)i * plane + (long long)sy * nx + sx]) + jump;
+    }
+    if (walls) {
+        if (y == 0) wall_bottom(d, k);
+        if (y == ny - 1) wall_top(d, k);
+    }
+}
+
+}  // namespace plbm

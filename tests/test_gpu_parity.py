@@ -1,0 +1,278 @@
+"""GPU path (through the C-ABI) against the FP64 oracle on the same seeded
+inputs: element-wise on lattices the oracle finishes in seconds, on the
+full named workloads where the oracle can run them, and on sampled nodes
+(light-cone windows) plus exact mode projections at the 8192^2 size."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import update_matrix as um
+import paper_2010_01847_gb300 as plbm
+from paper_2010_01847_gb300 import inputs
+from tests.helpers import TOL, check_gate, err_metrics, oracle_run, tau_pair
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+
+def gpu_run(nx, ny, tau_N, tau_R, fields, steps, bc_x=0, bc_y=0, delta_e=0.0,
+            precision="fp32", kernel="auto", graph_chunk=None):
+    lat = plbm.Lattice(nx, ny, tau_N, tau_R, bc_x, bc_y, delta_e, precision=precision,
+                       kernel=kernel, graph_chunk=graph_chunk)
+    lat.init(*fields)
+    if steps:
+        lat.step(steps)
+    return lat
+
+
+# (nx, ny, bc_x, bc_y, delta_e): several tiles, ragged tails, tiny edge cases
+LATTICES = [
+    (200, 72, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 2e-3),   # rows not a warp multiple
+    (256, 40, plbm.PERIODIC, plbm.PERIODIC, 0.0),
+    (96, 33, plbm.PERIODIC_GRADIENT, plbm.PERIODIC, -1e-3),
+    (37, 29, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3),    # ragged: scalar only
+    (3, 301, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3),    # Section 3.2 grid
+    (301, 3, plbm.PERIODIC, plbm.PERIODIC, 0.0),                   # Section 3.3 grid
+    (8, 2, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3),      # two wall rows only
+    (1, 1, plbm.PERIODIC, plbm.PERIODIC, 0.0),
+    (16, 1, plbm.PERIODIC_GRADIENT, plbm.PERIODIC, 1e-3),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16", "bf16"])
+@pytest.mark.parametrize("kernel", ["scalar", "vector", "auto"])
+@pytest.mark.parametrize("lattice", LATTICES, ids=lambda l: f"{l[0]}x{l[1]}_bc{l[2]}{l[3]}")
+def test_parity_small(lattice, kernel, precision):
+    nx, ny, bcx, bcy, de = lattice
+    vec = {"fp32": 4, "fp64": 2, "fp16": 8, "bf16": 8}[precision]
+    if kernel == "vector" and nx % vec:
+        pytest.skip("vector kernel needs nx % V == 0")
+    tau_N, tau_R = 0.9, 15.0
+    fields = inputs.random_state_fields(nx, ny, seed=nx * 1000 + ny)
+    steps = 57
+    g = gpu_run(nx, ny, tau_N, tau_R, fields, steps, bcx, bcy, de, precision, kernel)
+    o = oracle_run(nx, ny, tau_N, tau_R, fields, steps, bcx, bcy, de)
+    assert g.step_count == steps
+    # populations element by element (scaled by the deviation range)
+    fo = np.moveaxis(o.f, 2, 0)
+    dev = np.abs(fo - oracle.OMEGA[:, None, None] * fo.sum(0).mean()).max()
+    err_f = np.abs(g.populations() - fo).max() / dev
+    err_e, err_q = err_metrics(g.moments(), o.moments())
+    check_gate(precision, max(err_e, err_f), err_q)
+
+
+def test_step_zero_reports_initial_fields():
+    nx, ny = 64, 16
+    e, qx, qy = inputs.random_state_fields(nx, ny, seed=3)
+    g = gpu_run(nx, ny, 1.0, 4.0, (e, qx, qy), 0, precision="fp64")
+    o = oracle_run(nx, ny, 1.0, 4.0, (e, qx, qy), 0)
+    ge, gqx, gqy = g.moments()
+    oe, oqx, oqy = o.moments()
+    np.testing.assert_allclose(ge, oe, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(gqx, oqx, rtol=0, atol=1e-15)
+    g.step(0)
+    assert g.step_count == 0
+
+
+@pytest.mark.parametrize("tau_N,tau_R", [(math.inf, 3.0), (0.7, math.inf), (0.01, 0.02),
+                                         (50.0, 0.6)])
+def test_parity_degenerate_relaxation(tau_N, tau_R):
+    """Normal-only, resistive-only, tau just above 1/2, and huge tau_N."""
+    nx, ny = 128, 24
+    fields = inputs.random_state_fields(nx, ny, seed=11)
+    g = gpu_run(nx, ny, tau_N, tau_R, fields, 40, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS,
+                1e-3)
+    o = oracle_run(nx, ny, tau_N, tau_R, fields, 40, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS,
+                   1e-3)
+    err_e, err_q = err_metrics(g.moments(), o.moments())
+    assert err_e <= TOL["fp32"] and err_q <= TOL["fp32"], (err_e, err_q)
+
+
+def test_kernels_and_graph_chunks_agree_bitwise():
+    nx, ny = 512, 64
+    fields = inputs.random_state_fields(nx, ny, seed=5)
+    outs = []
+    for kernel, chunk in [("scalar", 0), ("vector", 0), ("vector", 64), ("auto", 16)]:
+        g = gpu_run(nx, ny, 0.8, 9.0, fields, 150, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS,
+                    1e-3, "fp32", kernel, graph_chunk=chunk)
+        outs.append(g.populations())
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+
+
+# --- the named workloads, full runs --------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_poiseuille_128x32_full(precision):
+    w = inputs.POISEUILLE_128x32
+    tau_N, tau_R = tau_pair(w.kn_N, w.kn_R, w.length)
+    fields = inputs.initial_fields(w)
+    g = gpu_run(w.nx, w.ny, tau_N, tau_R, fields, w.steps, w.bc_x, w.bc_y, w.delta_e, precision)
+    o = oracle_run(w.nx, w.ny, tau_N, tau_R, fields, w.steps, w.bc_x, w.bc_y, w.delta_e)
+    err_e, err_q = err_metrics(g.moments(), o.moments())
+    assert err_e <= TOL[precision] and err_q <= TOL[precision], (err_e, err_q)
+
+
+@pytest.mark.parametrize("kn_R", [0.1, 1.0, 10.0])
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_second_sound_4096x4_full(kn_R, precision):
+    w = inputs.second_sound_4096x4(kn_R)
+    tau_N, tau_R = tau_pair(w.kn_N, w.kn_R, w.length)
+    fields = inputs.initial_fields(w)
+    g = gpu_run(w.nx, w.ny, tau_N, tau_R, fields, w.steps, precision=precision)
+    o = oracle_run(w.nx, w.ny, tau_N, tau_R, fields, w.steps)
+    err_e, err_q = err_metrics(g.moments(), o.moments())
+    # 5000 near-steady steps: 16-bit rounding errors accumulate coherently
+    # (measured err_e ~0.3-1.2 for fp16); only finiteness is a hard check
+    check_gate(precision, err_e, err_q, sanity=10.0)
+
+
+# --- 8192^2: sampled nodes through light-cone windows ---------------------
+def _window(field, y0, x0, half):
+    ny, nx = field.shape
+    ys = (np.arange(y0 - half, y0 + half + 1)) % ny
+    xs = (np.arange(x0 - half, x0 + half + 1)) % nx
+    return np.ascontiguousarray(field[np.ix_(ys, xs)])
+
+
+@pytest.fixture(scope="module")
+def big_fields():
+    w = inputs.THROUGHPUT_8192
+    return w, inputs.initial_fields(w)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_8192_sampled_nodes_light_cone(big_fields, precision):
+    """After n steps a node depends only on nodes within n cells, so the oracle
+    on a periodic (2n+1)^2 window around a node gives its exact value."""
+    w, (e, qx, qy) = big_fields
+    tau_N, tau_R = tau_pair(w.kn_N, w.kn_R, w.length)
+    n = 24
+    g = gpu_run(w.nx, w.ny, tau_N, tau_R, (e, qx, qy), n, precision=precision)
+    ge, gqx, gqy = [t.cpu().numpy() for t in g.moments_device()]
+    rng = np.random.default_rng(1)
+    pts = [(0, 0), (w.ny - 1, w.nx - 1), (0, w.nx - 1), (w.ny - 1, 0)] + \
+        [tuple(p) for p in rng.integers(0, w.nx, (28, 2))]
+    res = []
+    for (y, x) in pts:
+        win = [_window(a, y, x, n) for a in (e, qx, qy)]
+        o = oracle_run(2 * n + 1, 2 * n + 1, tau_N, tau_R, win, n)
+        oe, oqx, oqy = o.moments()
+        res.append((ge[y, x], gqx[y, x], gqy[y, x], oe[n, n], oqx[n, n], oqy[n, n]))
+    res = np.array(res)
+    # deviation scale of e at this time, and the largest |q| in the sample
+    de = np.abs(res[:, 3] - 1.0).max()
+    dq = np.abs(res[:, 4:6]).max()
+    err_e = np.abs(res[:, 0] - res[:, 3]).max() / de
+    err_q = np.abs(res[:, 1:3] - res[:, 4:6]).max() / dq
+    check_gate(precision, err_e, err_q)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_8192_full_run_mode_projection_and_energy(big_fields, precision):
+    """2000 steps at full size: the (k=2pi/512, 0) Fourier amplitude of e
+    must follow the exact 8x8 mode matrix applied to the initial amplitude
+    (noise included), and total energy is conserved."""
+    w, (e, qx, qy) = big_fields
+    tau_N, tau_R = tau_pair(w.kn_N, w.kn_R, w.length)
+    g = gpu_run(w.nx, w.ny, tau_N, tau_R, (e, qx, qy), 0, precision=precision)
+    _, energy0 = g.residual()
+    g.step(w.steps)
+    r, energy = g.residual()
+    # 16-bit rounding does not conserve energy exactly (random sign per node)
+    assert energy == pytest.approx(energy0, rel={"bf16": 1e-9}.get(precision, 1e-10))
+    p = oracle.params(tau_N, tau_R)
+    k = 2 * np.pi / 512
+    x = torch.arange(w.nx, device=g.device, dtype=torch.float64)
+    phase = torch.exp(-1j * k * x)
+    et = g.moments_device()[0]
+    amp_g = ((et - 1.0).to(torch.complex128) * phase[None, :]).mean().item()
+    e0 = torch.from_numpy(e).to(g.device)
+    amp0 = ((e0 - 1.0).to(torch.complex128) * phase[None, :]).mean().item()
+    F0 = oracle.equilibrium(1.0, 0.0, 0.0) * amp0      # Eq. 15 with q = 0, per mode
+    Fn = np.linalg.matrix_power(um.mode_matrix(k, 0.0, p["tau"], p["tau_r"]), w.steps) @ F0
+    amp_exact = Fn.sum()
+    # 16-bit: informational beyond finiteness (errors grow ~ steps x u over 2000 steps)
+    check_gate(precision, abs(amp_g - amp_exact) / abs(amp_exact), 0.0, sanity=5.0)
+
+
+# --- residual, checkpoint, failure paths -----------------------------------
+def test_residual_matches_oracle_definition():
+    nx, ny, K = 96, 40, 25
+    fields = inputs.random_state_fields(nx, ny, seed=21)
+    args = (0.9, 12.0)
+    g = gpu_run(nx, ny, *args, fields, 0, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3,
+                "fp64")
+    r0, en0 = g.residual()
+    assert math.isinf(r0)
+    g.step(K)
+    r1, en1 = g.residual()
+    o = oracle_run(nx, ny, *args, fields, 0, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3)
+    a = o.moments()
+    assert en0 == pytest.approx(a[0].sum(), rel=1e-13)
+    o.step(K)
+    b = o.moments()
+    num = math.sqrt(sum(((x1 - x0) ** 2).sum() for x0, x1 in zip(a, b)))
+    den = math.sqrt(((b[0] - b[0].mean()) ** 2).sum() + (b[1] ** 2).sum() + (b[2] ** 2).sum())
+    assert r1 == pytest.approx(num / (K * den), rel=1e-9)
+    assert en1 == pytest.approx(b[0].sum(), rel=1e-13)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "fp64"])
+def test_checkpoint_resume_bitwise(precision):
+    nx, ny = 128, 48
+    fields = inputs.random_state_fields(nx, ny, seed=8)
+    args = (nx, ny, 0.8, 6.0, fields)
+    bc = (plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3)
+    full = gpu_run(*args, 100, *bc, precision)
+    part = gpu_run(*args, 37, *bc, precision)
+    blob = part.get_state()
+    fresh = plbm.Lattice(nx, ny, 0.8, 6.0, *bc, precision=precision)
+    fresh.set_state(blob)
+    assert fresh.step_count == 37
+    fresh.step(63)
+    assert np.array_equal(full.populations(), fresh.populations())
+
+
+def test_nonfinite_state_is_reported():
+    nx, ny = 64, 8
+    g = gpu_run(nx, ny, 1.0, 5.0, inputs.random_state_fields(nx, ny), 3)
+    blob = bytearray(g.get_state())
+    nbuf = 8 * nx * ny * 4
+    hdr = len(blob) - 2 * nbuf
+    cur = int(np.frombuffer(bytes(blob[32:36]), dtype=np.int32)[0])   # header field "cur"
+    at = hdr + cur * nbuf + 40                     # plane 0, node 10 of the live buffer
+    blob[at:at + 4] = np.array([np.nan], dtype=np.float32).tobytes()
+    g.set_state(bytes(blob))
+    g.step(5)
+    with pytest.raises(plbm.LBMError) as ex:
+        g.residual()
+    assert ex.value.status == plbm.ENONFINITE
+    with pytest.raises(plbm.LBMError) as ex:
+        g.init(np.full((ny, nx), np.nan))
+    assert ex.value.status == plbm.EINVAL
+
+
+def test_wrong_kernel_and_state_rejected():
+    g = gpu_run(37, 9, 1.0, 5.0, inputs.random_state_fields(37, 9), 1)
+    with pytest.raises(plbm.LBMError) as ex:
+        g.set_kernel("vector")
+    assert ex.value.status == plbm.EUNSUPPORTED
+    other = gpu_run(36, 9, 1.0, 5.0, inputs.random_state_fields(36, 9), 1)
+    with pytest.raises(plbm.LBMError):
+        g.set_state(other.get_state())
+
+
+def test_device_init_matches_host_init():
+    nx, ny = 256, 32
+    e, qx, qy = inputs.random_state_fields(nx, ny, seed=4)
+    a = gpu_run(nx, ny, 1.1, 7.0, (e, qx, qy), 20, precision="fp16")
+    b = plbm.Lattice(nx, ny, 1.1, 7.0, precision="fp16")
+    b.init(*[torch.from_numpy(v).cuda() for v in (e, qx, qy)])
+    b.step(20)
+    assert a.storage_scale == b.storage_scale
+    assert np.array_equal(a.populations(), b.populations())
