@@ -207,6 +207,42 @@ double lbm_storage_scale(const lbm_ctx *ctx);
  * lbm_create when ctx is NULL).  Never NULL; valid until the next call. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
+/* ---- Residual without device allocation ---------------------------------
+ * The paper has no counterpart to this call; it serves callers that must not
+ * allocate device memory while they run: a host application that reserved
+ * the device memory for its own pool at start-up and hands out nothing else,
+ * a plugin living inside a framework that owns the allocator, or a timing-
+ * critical loop that cannot afford cudaMalloc/cudaFree, which may
+ * synchronise the whole device.  Such a caller keeps its own moment fields
+ * (for example from lbm_moments_device) and asks for the same quantities
+ * lbm_residual returns.
+ *
+ * Inputs: e, qx, qy = DEVICE arrays of n_nodes float64 (e and q at step n);
+ * prev_e, prev_qx, prev_qy = the same at step n - k_steps, or all three NULL
+ * (then *r = +INFINITY).  e_ref = any finite reference (subtracted before the
+ * sums to keep them accurate; results do not depend on it up to rounding).
+ * Outputs (HOST, either may be NULL): r and total_energy with the definitions
+ * of lbm_residual.  Work is queued on `stream` (cudaStream_t, NULL = legacy
+ * default stream) on the current device; the call synchronises that stream.
+ *
+ * Memory: allocates nothing.  Its scratch is a fixed device array of
+ * 163,880 bytes inside the library, present on every device that loads the
+ * library until the process exits.  The first call on each device looks up
+ * that array's device address (with that device current) and caches it;
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents: calls that overlap on the GPU
+ * (different streams, or threads of one process) race and must be
+ * serialised by the caller.
+ * Limit: n_nodes <= LBM_NOALLOC_MAX_NODES (4096 x 4096 nodes).
+ * Errors (text from lbm_last_error(NULL)): EINVAL (NULL inputs, only some
+ * previous fields, n_nodes < 1 or above the limit, non-finite e_ref),
+ * ENONFINITE (a field holds NaN/Inf; outputs still written), ECUDA. */
+#define LBM_NOALLOC_MAX_NODES 16777216LL
+lbm_status lbm_residual_noalloc(const double *e, const double *qx, const double *qy,
+                                const double *prev_e, const double *prev_qx,
+                                const double *prev_qy, long long n_nodes, double e_ref,
+                                long k_steps, void *stream, double *r, double *total_energy);
+
 #ifdef __cplusplus
 }
 #endif

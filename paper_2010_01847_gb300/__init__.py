@@ -38,7 +38,9 @@ EXPORTS = [
     "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_step_count",
     "lbm_set_kernel", "lbm_get_kernel", "lbm_set_graph_chunk",
     "lbm_kernel_launches", "lbm_storage_scale", "lbm_last_error",
+    "lbm_residual_noalloc",
 ]
+NOALLOC_MAX_NODES = 16777216
 
 
 class LBMError(RuntimeError):
@@ -97,6 +99,8 @@ def load_library(path: str = LIB_PATH):
         "lbm_kernel_launches": (ctypes.c_longlong, [vp]),
         "lbm_storage_scale": (ctypes.c_double, [vp]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_residual_noalloc": (st, [vp, vp, vp, vp, vp, vp, ctypes.c_longlong,
+                                      ctypes.c_double, c_long, vp, dp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -109,6 +113,27 @@ def load_library(path: str = LIB_PATH):
 def tau_from_kn(kn: float, length: float) -> float:
     """Eq. 48 in lattice units: kn * length * sqrt(3/5)."""
     return load_library().lbm_tau_from_kn(float(kn), float(length))
+
+
+def residual_noalloc(fields, prev_fields=None, k_steps=0, e_ref=1.0, stream=None):
+    """lbm_residual_noalloc on CUDA float64 tensors: (r, total energy).
+    ``fields`` / ``prev_fields`` are (e, qx, qy) of equal size; the call
+    allocates no device memory."""
+    lib = load_library()
+    e, qx, qy = fields
+    n = e.numel()
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    prev = [ptr(t) for t in prev_fields] if prev_fields is not None else [None] * 3
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    r, en = ctypes.c_double(), ctypes.c_double()
+    st = lib.lbm_residual_noalloc(ptr(e), ptr(qx), ptr(qy), *prev, n, float(e_ref),
+                                  int(k_steps), ctypes.c_void_p(stream), ctypes.byref(r),
+                                  ctypes.byref(en))
+    if st != OK:
+        raise LBMError(st, lib.lbm_last_error(None).decode())
+    return r.value, en.value
 
 
 def _dptr(a: np.ndarray):

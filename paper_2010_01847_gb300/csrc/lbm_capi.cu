@@ -363,6 +363,8 @@ lbm_status build_graph(lbm_ctx *c, int start) {
 
 }  // namespace
 
+void plbm::set_global_error(const char *msg) { g_create_error = msg; }
+
 extern "C" {
 
 double lbm_tau_from_kn(double kn, double length) { return kn * length * std::sqrt(3.0 / 5.0); }

@@ -10,6 +10,9 @@ namespace plbm {
 enum { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2, PREC_FP64 = 3 };
 enum { KERNEL_AUTO = 0, KERNEL_SCALAR = 1, KERNEL_VECTOR = 2, KERNEL_STAGED = 3 };
 
+// Sets the text lbm_last_error(NULL) returns.
+void set_global_error(const char *msg);
+
 // Elements per 16-byte vector for a storage kind.
 int vector_width(int precision);
 
