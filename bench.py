@@ -6,7 +6,7 @@ Kn_R = 0.1 measured on the 512-cell wavelength, populations stored as FP32
 deviations (``--precision`` selects fp16/bf16/fp64 storage).  One bench
 step = one time step of Eq. 13 over the whole lattice (pull-stream, seam and
 wall rules, collision); the FP64 residual / energy reduction runs every 100
-steps inside the timed region.  The population buffers (2 x 2.1 GB) exceed
+steps inside the timed region, fused into that step's launch.  The population buffers (2 x 2.1 GB) exceed
 the 129 MB L2, so no flush is needed between steps.
 
 Metric: GLUPS (10^9 lattice-site updates per second, whole job).  Also
@@ -276,27 +276,33 @@ def run_native(args):
 
     lat = plbm.Lattice(nx, ny, tau_N, tau_R, precision=args.precision, kernel=args.kernel)
     lat.init(e_dev, z_dev, z_dev)
+    tuned = None
+    if args.kernel == "auto":
+        # set-up, untimed: pick the fastest kernel / staged shape on this GPU
+        tuned = lat.autotune(20)
     stream = torch.cuda.current_stream(dev)
 
     def chunked(nsteps, events=None):
-        """Advance nsteps with the residual every RESIDUAL_EVERY steps;
-        record events around each run of stream-collide launches."""
+        """Advance nsteps; every RESIDUAL_EVERY-th step also reduces the
+        residual inside its stream-collide launch (lbm_step_residual).
+        Events bracket each run of plain stream-collide launches."""
         done = 0
         launches = 0
         while done < nsteps:
             k = min(RESIDUAL_EVERY, nsteps - done)
+            plain = k - 1 if k == RESIDUAL_EVERY else k
             if events is not None:
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-            lat.step(k)
+            lat.step(plain)
             if events is not None:
                 b.record(stream)
-                events.append((a, b, k))
-            launches += k
+                events.append((a, b, plain))
+            launches += plain
+            if plain < k:
+                lat.step_residual(1)
+                launches += 2          # fused step + fixed-order finalize
             done += k
-            if done % RESIDUAL_EVERY == 0:
-                lat.residual()
-                launches += 2
         return launches
 
     chunked(max(args.warmup, 3))
@@ -381,6 +387,8 @@ def run_native(args):
                        "kn_N": w["kn_N"], "kn_R": w["kn_R"], "length_cells": w["length"],
                        "storage": f"{args.precision} deviation" if args.precision != "fp64"
                        else "fp64 deviation", "kernel": lat.kernel,
+                       "staged_shape": lat.staged_config if lat.kernel == "staged" else None,
+                       "autotuned": tuned is not None,
                        "residual_every": RESIDUAL_EVERY,
                        "l2": "inputs larger than L2 (2 x population buffers >> 129 MB); "
                              "no flush", "parallelism": f"replicas x{world}"},

@@ -85,8 +85,10 @@ typedef enum {
     LBM_KERNEL_AUTO = 0,     /* fastest kernel valid for the lattice          */
     LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx                   */
     LBM_KERNEL_VECTOR = 2,   /* 16-byte vectors along x; nx % (16/size) == 0  */
-    LBM_KERNEL_STAGED = 3    /* bulk-copy (TMA engine) row staging in shared  */
-                             /* memory; same condition as VECTOR              */
+    LBM_KERNEL_STAGED = 3    /* bulk asynchronous copies (TMA engine) of row  */
+                             /* segments into a shared-memory ring; needs nx  */
+                             /* a multiple of the tile width (4096/size with  */
+                             /* the default shape)                            */
 } lbm_kernel;
 
 typedef struct {
@@ -151,7 +153,8 @@ lbm_status lbm_init_device(lbm_ctx *ctx, const double *e, const double *qx,
  * not initialised), ECUDA (launch failure). */
 lbm_status lbm_step(lbm_ctx *ctx, long n);
 
-/* Wait for the context's stream; ECUDA if a queued kernel failed. */
+/* Wait for the context's stream; ECUDA if a queued kernel failed, ETIMEOUT
+ * if a bounded device-side wait of the staged kernel gave up. */
 lbm_status lbm_sync(lbm_ctx *ctx);
 
 /* e (Eq. 53) and q (Eq. 54) of the state at the current step, into HOST
@@ -166,14 +169,25 @@ lbm_status lbm_moments_device(lbm_ctx *ctx, double *e, double *qx,
  * as float64 HOST array [8][ny][nx].  Synchronous. */
 lbm_status lbm_populations(lbm_ctx *ctx, double *f);
 
-/* Convergence residual and total energy, reduced in FP64 on the device.
+/* Convergence residual and total energy, summed in FP64 on the device
+ * (per-node e and q formed in the compute precision).
  *   r = ||(e, q)^n - (e, q)^m||_2 / ((n - m) ||(e - mean(e), q)^n||_2)
  * where m is the step of the previous lbm_residual call since lbm_init
  * (r = +INFINITY on the first call or when n == m), and
  *   total_energy = sum over nodes of e (Eq. 53).
  * Either output may be NULL.  Synchronous.  Errors: ENONFINITE when any
- * e or q is NaN/Inf (outputs still written), ECUDA. */
+ * e or q is NaN/Inf (outputs still written), ETIMEOUT when a bounded wait of
+ * the staged kernel gave up since lbm_init, ECUDA. */
 lbm_status lbm_residual(lbm_ctx *ctx, double *r, double *total_energy);
+
+/* Advance n >= 0 steps and return r and total_energy of the state at the
+ * final step, exactly as lbm_step(n) followed by lbm_residual would (same
+ * history, same definitions), but with the residual sums reduced inside the
+ * last step's stream-collide launch instead of a separate pass over the
+ * lattice.  Per-node moments are formed in the compute precision and summed
+ * in FP64.  n = 0 is lbm_residual.  Synchronous.  Errors as lbm_step and
+ * lbm_residual. */
+lbm_status lbm_step_residual(lbm_ctx *ctx, long n, double *r, double *total_energy);
 
 /* Checkpoint: an opaque host blob of lbm_state_bytes(ctx) bytes holding the
  * raw population buffers, the step count and the storage scale.
@@ -192,6 +206,33 @@ lbm_status lbm_set_kernel(lbm_ctx *ctx, int kernel);
 
 /* The kernel lbm_step will launch (never LBM_KERNEL_AUTO). */
 int lbm_get_kernel(const lbm_ctx *ctx);
+
+/* Launch shape of the staged kernel; results do not depend on it.
+ *   stages          shared-memory ring depth, 2..6 (0 = default 2)
+ *   ctas_per_sm     persistent CTAs per SM (0 = as many as fit)
+ *   consumer_warps  4 or 8 (0 = 8): tile width 32 x consumer_warps x
+ *                   (16 / element size) nodes; nx must be a multiple of it
+ *   l2_evict_first  nonzero: the bulk loads carry an L2 evict-first policy
+ * EUNSUPPORTED when the shape cannot be launched for this lattice/device. */
+lbm_status lbm_set_staged_config(lbm_ctx *ctx, int stages, int ctas_per_sm,
+                                 int consumer_warps, int l2_evict_first);
+
+/* The staged kernel's current shape and persistent grid size (any output
+ * may be NULL). */
+lbm_status lbm_get_staged_config(const lbm_ctx *ctx, int *stages, int *ctas_per_sm,
+                                 int *consumer_warps, int *l2_evict_first, int *grid);
+
+/* Autotuner: times every stream-collide kernel and staged shape that can
+ * run this lattice (vector or scalar; staged with 2 or 3 stages and 8 or 4
+ * consumer warps), trial_steps steps each (0 = 20) after 2 warm-up steps,
+ * on the context's stream, and keeps the fastest for later lbm_step calls.
+ * The timings run on the context's own buffers; when the context holds a
+ * state (after lbm_init) both buffers are first copied to a temporary
+ * device allocation (2 x lbm_population_bytes) and restored afterwards, so
+ * the state and the step count are unchanged.  Outputs (may be NULL): the
+ * chosen LBM_KERNEL_* and its mean time per step in microseconds.
+ * Synchronous. */
+lbm_status lbm_autotune(lbm_ctx *ctx, int trial_steps, int *kernel, double *us_per_step);
 
 /* Steps per captured CUDA graph chunk (even, >= 2), or 0 to launch every
  * step directly.  Default 64. */

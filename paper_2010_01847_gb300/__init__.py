@@ -35,8 +35,10 @@ EXPORTS = [
     "lbm_tau_from_kn", "lbm_population_bytes", "lbm_create", "lbm_create_ex",
     "lbm_destroy", "lbm_init", "lbm_init_device", "lbm_step", "lbm_sync",
     "lbm_moments", "lbm_moments_device", "lbm_populations", "lbm_residual",
+    "lbm_step_residual",
     "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_step_count",
-    "lbm_set_kernel", "lbm_get_kernel", "lbm_set_graph_chunk",
+    "lbm_set_kernel", "lbm_get_kernel", "lbm_set_staged_config", "lbm_get_staged_config",
+    "lbm_set_graph_chunk", "lbm_autotune",
     "lbm_kernel_launches", "lbm_storage_scale", "lbm_last_error",
     "lbm_residual_noalloc",
 ]
@@ -89,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_moments_device": (st, [vp, vp, vp, vp]),
         "lbm_populations": (st, [vp, dp]),
         "lbm_residual": (st, [vp, dp, dp]),
+        "lbm_step_residual": (st, [vp, c_long, dp, dp]),
         "lbm_state_bytes": (c_size, [vp]),
         "lbm_get_state": (st, [vp, vp, c_size]),
         "lbm_set_state": (st, [vp, vp, c_size]),
@@ -96,6 +99,10 @@ def load_library(path: str = LIB_PATH):
         "lbm_set_kernel": (st, [vp, ctypes.c_int]),
         "lbm_get_kernel": (ctypes.c_int, [vp]),
         "lbm_set_graph_chunk": (st, [vp, ctypes.c_int]),
+        "lbm_autotune": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
+        "lbm_set_staged_config": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int]),
+        "lbm_get_staged_config": (st, [vp] + [ctypes.POINTER(ctypes.c_int)] * 5),
         "lbm_kernel_launches": (ctypes.c_longlong, [vp]),
         "lbm_storage_scale": (ctypes.c_double, [vp]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
@@ -279,6 +286,14 @@ class Lattice:
         self._check(st)
         return r.value, en.value
 
+    def step_residual(self, n: int):
+        """Advance n steps; (r, total energy) of the final state, reduced
+        inside the last step's launch (see lbm_step_residual)."""
+        r, en = ctypes.c_double(), ctypes.c_double()
+        st = self._lib.lbm_step_residual(self._ctx, int(n), ctypes.byref(r), ctypes.byref(en))
+        self._check(st)
+        return r.value, en.value
+
     def get_state(self) -> bytes:
         n = self._lib.lbm_state_bytes(self._ctx)
         buf = ctypes.create_string_buffer(n)
@@ -309,6 +324,27 @@ class Lattice:
     def kernel(self) -> str:
         k = self._lib.lbm_get_kernel(self._ctx)
         return {v: n for n, v in KERNELS.items()}[k]
+
+    def autotune(self, trial_steps: int = 20):
+        """Pick the fastest kernel / staged shape for this lattice by timing
+        (state preserved); returns (kernel name, us per step)."""
+        k, us = ctypes.c_int(), ctypes.c_double()
+        self._check(self._lib.lbm_autotune(self._ctx, int(trial_steps), ctypes.byref(k),
+                                           ctypes.byref(us)))
+        return {v: n for n, v in KERNELS.items()}[k.value], us.value
+
+    def set_staged_config(self, stages: int = 0, ctas_per_sm: int = 0, consumer_warps: int = 0,
+                          l2_evict_first: bool = False):
+        """Shape of the staged kernel (0 = default); see lbm_set_staged_config."""
+        self._check(self._lib.lbm_set_staged_config(self._ctx, int(stages), int(ctas_per_sm),
+                                                    int(consumer_warps), int(l2_evict_first)))
+
+    @property
+    def staged_config(self):
+        v = [ctypes.c_int() for _ in range(5)]
+        self._check(self._lib.lbm_get_staged_config(self._ctx, *[ctypes.byref(x) for x in v]))
+        keys = ("stages", "ctas_per_sm", "consumer_warps", "l2_evict_first", "grid")
+        return dict(zip(keys, (x.value for x in v)))
 
     def set_graph_chunk(self, steps: int):
         self._check(self._lib.lbm_set_graph_chunk(self._ctx, int(steps)))

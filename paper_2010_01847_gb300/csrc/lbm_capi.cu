@@ -31,16 +31,18 @@ struct lbm_ctx {
     long n = 0;            // steps since lbm_init
     bool initialised = false;
     int kernel = KERNEL_SCALAR;
+    StagedPlan plan;            // launch shape of the staged kernel
+    int stages_req = 0, ctas_req = 0, cw_req = 0, hint_req = 0;
     int graph_chunk = 64;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    double *prev = nullptr;     // residual history, 3 planes of doubles
+    void *prev = nullptr;       // residual history, 3 planes of the compute type
     bool have_prev = false;
     long prev_step = 0;
     double *fields = nullptr;   // 3 planes of doubles: init staging / read-outs
-    double *partials = nullptr;
-    double *sums = nullptr;
-    unsigned long long *maxbits = nullptr;
+    double *partials = nullptr; // 5 doubles per block of the widest reduction launch
+    long long partial_blocks = 0;
+    double *aux = nullptr;      // [0..4] sums, [5] max-deviation bits, [6] status word
     long long launches = 0;
     std::string err;
 };
@@ -78,6 +80,9 @@ lbm_status fail(lbm_ctx *ctx, lbm_status s, const std::string &msg) {
 lbm_status cuda_fail(lbm_ctx *ctx, cudaError_t e, const char *where) {
     std::string msg = std::string(where) + ": " + cudaGetErrorName(e) + " (" +
                       cudaGetErrorString(e) + ")";
+    // the error is reported here; clear the runtime's per-thread record of it
+    // so a later call does not pick it up again (sticky errors persist anyway)
+    (void)cudaGetLastError();
     if (e == cudaErrorMemoryAllocation) return fail(ctx, LBM_ENOMEM, msg);
     return fail(ctx, LBM_ECUDA, msg);
 }
@@ -142,11 +147,29 @@ cudaError_t dispatch(const lbm_ctx *c, A... a) {
     }
 }
 
+int *status_word(const lbm_ctx *c) { return (int *)(c->aux + 6); }
+double *sums_ptr(const lbm_ctx *c) { return c->aux; }
+
 template <typename T> struct StepOp {
     static cudaError_t run(const lbm_ctx *c, int src, cudaStream_t s) {
         using C = typename Store<T>::C;
         return launch_step<T>(c->kernel, (const T *)c->buf[src], (T *)c->buf[1 - src], c->nx,
-                              c->ny, c->bc_x, c->bc_y, make_coef<C>(c), s);
+                              c->ny, c->bc_x, c->bc_y, make_coef<C>(c), status_word(c), nullptr,
+                              c->plan, nullptr, s);
+    }
+};
+// One step that also reduces the residual sums of the state it pulls.
+template <typename T> struct StepResidualOp {
+    static cudaError_t run(const lbm_ctx *c, int src, int *blocks) {
+        using C = typename Store<T>::C;
+        ResidualReq<C> rq;
+        rq.prev = (C *)c->prev;
+        rq.have_prev = c->have_prev ? 1 : 0;
+        rq.inv_scale = (C)(1.0 / c->scale);
+        rq.partials = c->partials;
+        return launch_step<T>(c->kernel, (const T *)c->buf[src], (T *)c->buf[1 - src], c->nx,
+                              c->ny, c->bc_x, c->bc_y, make_coef<C>(c), status_word(c), &rq,
+                              c->plan, blocks, c->stream);
     }
 };
 template <typename T> struct MomentsOp {
@@ -168,8 +191,8 @@ template <typename T> struct ResidualOp {
         (void)dummy;
         using C = typename Store<T>::C;
         return launch_residual<T>((const T *)c->buf[1 - c->cur], make_readout(c),
-                                  make_coef<C>(c), c->prev, c->have_prev, c->partials, c->sums,
-                                  c->stream);
+                                  make_coef<C>(c), (C *)c->prev, c->have_prev, c->partials,
+                                  sums_ptr(c), c->stream);
     }
 };
 template <typename T> struct InitOp {
@@ -189,24 +212,80 @@ void drop_graphs(lbm_ctx *c) {
     }
 }
 
+size_t compute_size(int precision) { return precision == PREC_FP64 ? 8 : 4; }
+
 lbm_status ensure_scratch(lbm_ctx *c, bool need_prev) {
     if (!c->fields) CK(c, cudaMalloc(&c->fields, sizeof(double) * 3 * (size_t)c->plane));
-    if (!c->partials) CK(c, cudaMalloc(&c->partials, sizeof(double) * 5 * RESIDUAL_BLOCKS));
-    if (!c->sums) CK(c, cudaMalloc(&c->sums, sizeof(double) * 5));
-    if (!c->maxbits) CK(c, cudaMalloc(&c->maxbits, sizeof(unsigned long long)));
-    if (need_prev && !c->prev)
-        CK(c, cudaMalloc(&c->prev, sizeof(double) * 3 * (size_t)c->plane));
+    if (!c->aux) {
+        CK(c, cudaMalloc(&c->aux, sizeof(double) * 8));
+        CK(c, cudaMemset(c->aux, 0, sizeof(double) * 8));
+    }
+    if (need_prev) {
+        long long blocks = step_blocks(c->kernel, c->precision, c->nx, c->ny, c->plan);
+        if (blocks < RESIDUAL_BLOCKS) blocks = RESIDUAL_BLOCKS;
+        if (blocks > c->partial_blocks) {
+            cudaFree(c->partials);
+            c->partials = nullptr;
+            c->partial_blocks = 0;
+            CK(c, cudaMalloc(&c->partials, sizeof(double) * 5 * (size_t)blocks));
+            c->partial_blocks = blocks;
+        }
+        if (!c->prev)
+            CK(c, cudaMalloc(&c->prev, compute_size(c->precision) * 3 * (size_t)c->plane));
+    }
     return LBM_OK;
 }
 
-int resolve_kernel(const lbm_ctx *c, int requested) {
+// Reads the device status word (after the stream is synchronised).
+lbm_status check_status(lbm_ctx *c) {
+    if (!c->aux) return LBM_OK;
+    int st = 0;
+    CK(c, cudaMemcpy(&st, status_word(c), sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) return fail(c, LBM_ETIMEOUT, "a bounded device-side wait gave up (staged kernel)");
+    return LBM_OK;
+}
+
+// Residual and energy from the 5 device sums (same formulas for the
+// stand-alone and the fused pass).
+lbm_status finish_residual(lbm_ctx *c, const double (&sums)[5], double *r,
+                           double *total_energy) {
+    const double n = (double)c->plane;
+    const double mean = sums[0] / n;
+    const double var_e = std::fmax(sums[1] - n * mean * mean, 0.0);
+    const double denom = std::sqrt(var_e + sums[2]);
+    const long k = c->n - c->prev_step;
+    double res = INFINITY;
+    if (c->have_prev && k > 0) {
+        const double num = std::sqrt(sums[3]);
+        res = denom > 0.0 ? num / ((double)k * denom) : (num == 0.0 ? 0.0 : INFINITY);
+    }
+    c->have_prev = true;
+    c->prev_step = c->n;
+    if (r) *r = res;
+    if (total_energy) *total_energy = n * c->e_ref + sums[0];
+    if (sums[4] > 0.0) return fail(c, LBM_ENONFINITE, "state holds NaN or Inf");
+    return LBM_OK;
+}
+
+int resolve_kernel(lbm_ctx *c, int requested) {
     const bool vec_ok = c->nx % vector_width(c->precision) == 0;
+    // the staged kernel also needs its plan (launch attributes, occupancy)
+    // worked out on this device, here, outside any stream capture
+    const int cw = c->cw_req > 0 ? c->cw_req : 8;
+    bool staged_ok = staged_supported(c->precision, c->nx, c->ny, cw);
+    if (staged_ok) {
+        StagedPlan p;
+        staged_ok = staged_plan(c->precision, c->stages_req, c->ctas_req, cw, c->hint_req, &p) ==
+                    cudaSuccess;
+        if (staged_ok) c->plan = p;
+        else (void)cudaGetLastError();
+    }
     if (requested == KERNEL_AUTO) {
-        if (staged_supported(c->precision, c->nx, c->ny)) return KERNEL_STAGED;
+        if (staged_ok) return KERNEL_STAGED;
         return vec_ok ? KERNEL_VECTOR : KERNEL_SCALAR;
     }
     if (requested == KERNEL_VECTOR && !vec_ok) return -1;
-    if (requested == KERNEL_STAGED && !staged_supported(c->precision, c->nx, c->ny)) return -1;
+    if (requested == KERNEL_STAGED && !staged_ok) return -1;
     return requested;
 }
 
@@ -263,7 +342,6 @@ lbm_status create_common(lbm_grid g, double tau_N, double tau_R, lbm_boundary bc
     c->e_ref = e_ref;
     c->stream = (cudaStream_t)stream;
     c->buf_bytes = lbm_population_bytes(g, precision);
-    c->kernel = resolve_kernel(c, KERNEL_AUTO);
 
     if (buf_a || buf_b) {
         if (!buf_a || !buf_b || buf_a == buf_b) {
@@ -299,16 +377,18 @@ lbm_status create_common(lbm_grid g, double tau_N, double tau_R, lbm_boundary bc
         lbm_destroy(c);
         return s;
     }
+    c->kernel = resolve_kernel(c, KERNEL_AUTO);
     *out = c;
     return LBM_OK;
 }
 
 lbm_status init_from_device(lbm_ctx *c, const double *e, const double *qx, const double *qy) {
     if (lbm_status s = ensure_scratch(c, false)) return s;
-    CK(c, cudaMemsetAsync(c->maxbits, 0, sizeof(unsigned long long), c->stream));
-    CK(c, launch_max_deviation(e, qx, qy, c->plane, c->e_ref, c->maxbits, c->stream));
+    unsigned long long *maxbits = (unsigned long long *)(c->aux + 5);
+    CK(c, cudaMemsetAsync(c->aux, 0, sizeof(double) * 8, c->stream));   // also clears status
+    CK(c, launch_max_deviation(e, qx, qy, c->plane, c->e_ref, maxbits, c->stream));
     unsigned long long bits = 0;
-    CK(c, cudaMemcpyAsync(&bits, c->maxbits, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&bits, maxbits, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     double amax;
     std::memcpy(&amax, &bits, sizeof(amax));
@@ -401,8 +481,7 @@ void lbm_destroy(lbm_ctx *c) {
     cudaFree(c->prev);
     cudaFree(c->fields);
     cudaFree(c->partials);
-    cudaFree(c->sums);
-    cudaFree(c->maxbits);
+    cudaFree(c->aux);
     delete c;
 }
 
@@ -459,7 +538,7 @@ lbm_status lbm_sync(lbm_ctx *c) {
     DeviceGuard g(c->device);
     CK(c, cudaStreamSynchronize(c->stream));
     CK(c, cudaGetLastError());
-    return LBM_OK;
+    return check_status(c);
 }
 
 lbm_status lbm_moments_device(lbm_ctx *c, double *e, double *qx, double *qy) {
@@ -513,24 +592,31 @@ lbm_status lbm_residual(lbm_ctx *c, double *r, double *total_energy) {
     if (lbm_status s = ensure_scratch(c, true)) return s;
     CK(c, dispatch<ResidualOp>(c, 0));
     double sums[5];
-    CK(c, cudaMemcpyAsync(sums, c->sums, sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(sums, sums_ptr(c), sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    const double n = (double)c->plane;
-    const double mean = sums[0] / n;
-    const double var_e = std::fmax(sums[1] - n * mean * mean, 0.0);
-    const double denom = std::sqrt(var_e + sums[2]);
-    const long k = c->n - c->prev_step;
-    double res = INFINITY;
-    if (c->have_prev && k > 0) {
-        const double num = std::sqrt(sums[3]);
-        res = denom > 0.0 ? num / ((double)k * denom) : (num == 0.0 ? 0.0 : INFINITY);
-    }
-    c->have_prev = true;
-    c->prev_step = c->n;
-    if (r) *r = res;
-    if (total_energy) *total_energy = n * c->e_ref + sums[0];
-    if (sums[4] > 0.0) return fail(c, LBM_ENONFINITE, "state holds NaN or Inf");
-    return LBM_OK;
+    if (lbm_status s = check_status(c)) return s;
+    return finish_residual(c, sums, r, total_energy);
+}
+
+lbm_status lbm_step_residual(lbm_ctx *c, long n, double *r, double *total_energy) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+    if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    if (n == 0) return lbm_residual(c, r, total_energy);
+    DeviceGuard g(c->device);
+    if (lbm_status s = ensure_scratch(c, true)) return s;
+    if (lbm_status s = lbm_step(c, n - 1)) return s;
+    int blocks = 0;
+    CK(c, dispatch<StepResidualOp>(c, c->cur, &blocks));
+    c->cur = 1 - c->cur;
+    c->n += 1;
+    c->launches += 1;
+    CK(c, launch_finalize(c->partials, blocks, sums_ptr(c), c->stream));
+    double sums[5];
+    CK(c, cudaMemcpyAsync(sums, sums_ptr(c), sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (lbm_status s = check_status(c)) return s;
+    return finish_residual(c, sums, r, total_energy);
 }
 
 size_t lbm_state_bytes(const lbm_ctx *c) {
@@ -612,6 +698,42 @@ lbm_status lbm_set_kernel(lbm_ctx *c, int kernel) {
 
 int lbm_get_kernel(const lbm_ctx *c) { return c ? c->kernel : -1; }
 
+lbm_status lbm_set_staged_config(lbm_ctx *c, int stages, int ctas_per_sm, int consumer_warps,
+                                 int l2_evict_first) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (stages < 0 || ctas_per_sm < 0 || consumer_warps < 0)
+        return fail(c, LBM_EINVAL, "negative configuration");
+    const int cw = consumer_warps > 0 ? consumer_warps : 8;
+    if (!staged_supported(c->precision, c->nx, c->ny, cw))
+        return fail(c, LBM_EUNSUPPORTED, "nx is not a multiple of the staged tile width");
+    DeviceGuard g(c->device);
+    StagedPlan p;
+    cudaError_t e = staged_plan(c->precision, stages, ctas_per_sm, cw, l2_evict_first, &p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(c, LBM_EUNSUPPORTED, std::string("staged configuration not possible: ") +
+                                             cudaGetErrorString(e));
+    }
+    drop_graphs(c);
+    c->stages_req = stages;
+    c->ctas_req = ctas_per_sm;
+    c->cw_req = cw;
+    c->hint_req = l2_evict_first ? 1 : 0;
+    c->plan = p;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_staged_config(const lbm_ctx *c, int *stages, int *ctas_per_sm,
+                                 int *consumer_warps, int *l2_evict_first, int *grid) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (stages) *stages = c->plan.stages;
+    if (ctas_per_sm) *ctas_per_sm = c->plan.ctas_per_sm;
+    if (consumer_warps) *consumer_warps = c->plan.consumer_warps;
+    if (l2_evict_first) *l2_evict_first = c->plan.hint;
+    if (grid) *grid = c->plan.grid;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_graph_chunk(lbm_ctx *c, int steps) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (steps < 0 || steps == 1 || (steps & 1))
@@ -619,6 +741,92 @@ lbm_status lbm_set_graph_chunk(lbm_ctx *c, int steps) {
     DeviceGuard g(c->device);
     drop_graphs(c);
     c->graph_chunk = steps;
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per_step) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (trial_steps < 0) return fail(c, LBM_EINVAL, "trial_steps must be >= 0");
+    if (trial_steps == 0) trial_steps = 20;
+    if (trial_steps & 1) ++trial_steps;       // even: the buffers end where they began
+    DeviceGuard g(c->device);
+    if (lbm_status s = ensure_scratch(c, false)) return s;   // the status word
+    struct Cand { int kernel, stages, cw; };
+    Cand cands[8];
+    int nc = 0;
+    if (c->nx % vector_width(c->precision) == 0) cands[nc++] = {KERNEL_VECTOR, 0, 0};
+    else cands[nc++] = {KERNEL_SCALAR, 0, 0};
+    for (int cw : {8, 4})
+        if (staged_supported(c->precision, c->nx, c->ny, cw))
+            for (int st : {2, 3}) cands[nc++] = {KERNEL_STAGED, st, cw};
+
+    // keep the state: copy both buffers aside when the lattice holds one
+    void *saved = nullptr;
+    if (c->initialised) {
+        CK(c, cudaMallocAsync(&saved, 2 * c->buf_bytes, c->stream));
+        for (int i = 0; i < 2; ++i)
+            CK(c, cudaMemcpyAsync((char *)saved + i * c->buf_bytes, c->buf[i], c->buf_bytes,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+    }
+    const int old_kernel = c->kernel;
+    const StagedPlan old_plan = c->plan;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    float best = 0.f;
+    int best_i = -1;
+    StagedPlan best_plan = c->plan;
+    for (int i = 0; i < nc && err == cudaSuccess; ++i) {
+        StagedPlan p = c->plan;
+        if (cands[i].kernel == KERNEL_STAGED &&
+            staged_plan(c->precision, cands[i].stages, 0, cands[i].cw, 0, &p) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        c->kernel = cands[i].kernel;
+        c->plan = p;
+        for (int s = 0; s < 2 && err == cudaSuccess; ++s)      // warm-up
+            err = dispatch<StepOp>(c, s & 1, c->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+        for (int s = 0; s < trial_steps && err == cudaSuccess; ++s)
+            err = dispatch<StepOp>(c, s & 1, c->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && (best_i < 0 || ms < best)) {
+            best = ms;
+            best_i = i;
+            best_plan = p;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (saved) {
+        for (int i = 0; i < 2 && err == cudaSuccess; ++i)
+            err = cudaMemcpyAsync(c->buf[i], (char *)saved + i * c->buf_bytes, c->buf_bytes,
+                                  cudaMemcpyDeviceToDevice, c->stream);
+        cudaFreeAsync(saved, c->stream);
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    if (err != cudaSuccess || best_i < 0) {
+        c->kernel = old_kernel;
+        c->plan = old_plan;
+        return err != cudaSuccess ? cuda_fail(c, err, "lbm_autotune")
+                                  : fail(c, LBM_ECUDA, "no kernel could be timed");
+    }
+    if (lbm_status s = check_status(c)) return s;
+    drop_graphs(c);
+    c->kernel = cands[best_i].kernel;
+    c->plan = best_plan;
+    if (cands[best_i].kernel == KERNEL_STAGED) {
+        c->stages_req = cands[best_i].stages;
+        c->ctas_req = 0;
+        c->cw_req = cands[best_i].cw;
+        c->hint_req = 0;
+    }
+    if (kernel) *kernel = c->kernel;
+    if (us_per_step) *us_per_step = 1000.0 * best / trial_steps;
     return LBM_OK;
 }
 

@@ -146,4 +146,74 @@ __device__ __forceinline__ void pull_node(const T *__restrict__ src, long long p
     }
 }
 
+// Residual contribution of one node of the state at step n (pulled, after
+// the boundary, before collision).  de = e - e_ref and q are formed in the
+// compute type C; each node's terms are added to the FP64 accumulators acc,
+// and compared with / written to the history planes prev (3 planes of C:
+// de, qx, qy at the previous residual):
+//   acc[0] += de, acc[1] += de^2, acc[2] += |q|^2,
+//   acc[3] += |(de, q) - prev|^2, acc[4] += 1 if a value is not finite.
+// Every kernel that reduces a residual uses this function, so the per-node
+// terms are bit-identical between them; only the FP64 summation order
+// differs.
+template <typename C>
+__device__ __forceinline__ void residual_node(const C (&d)[8], const Coef<C> &k, C inv_s,
+                                              C *__restrict__ prev, long long n,
+                                              long long node, bool have_prev,
+                                              double (&acc)[5]) {
+    const C rho = ((d[0] + d[2]) + (d[1] + d[3])) + ((d[4] + d[6]) + (d[5] + d[7]));
+    const C mx = (d[0] - d[2]) + (d[4] - d[6]) + (d[7] - d[5]);
+    const C my = (d[1] - d[3]) + (d[4] - d[6]) + (d[5] - d[7]);
+    const C de = rho * inv_s;
+    const C qx = (mx - k.lambda * mx) * inv_s;
+    const C qy = (my - k.lambda * my) * inv_s;
+    if (!(isfinite(de) && isfinite(qx) && isfinite(qy))) acc[4] += 1.0;
+    acc[0] += (double)de;
+    acc[1] += (double)(de * de);
+    acc[2] += (double)(qx * qx + qy * qy);
+    if (have_prev) {
+        const C a = de - prev[node], b = qx - prev[n + node], c = qy - prev[2 * n + node];
+        acc[3] += (double)(a * a + b * b + c * c);
+    }
+    prev[node] = de;
+    prev[n + node] = qx;
+    prev[2 * n + node] = qy;
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of 5 doubles per thread (every thread of the block must
+// call it); thread 0 writes the block's sums to out[0..4].
+__device__ __forceinline__ void block_sum5_store(const double (&v)[5], double *out) {
+    __shared__ double sh[5][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const double w = warp_sum_f64(v[q]);
+        if (lane == 0) sh[q][warp] = w;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const double w = warp_sum_f64(lane < nw ? sh[q][lane] : 0.0);
+            if (lane == 0) out[q] = w;
+        }
+    }
+}
+
+// Request for the fused residual in a step launch.
+template <typename C>
+struct ResidualReq {
+    C *prev;            // history planes (3 x n of C), read and overwritten
+    int have_prev;      // compare with the history
+    C inv_scale;        // 1 / storage scale
+    double *partials;   // 5 doubles per block of the launch
+};
+
 }  // namespace plbm

@@ -16,17 +16,48 @@ void set_global_error(const char *msg);
 // Elements per 16-byte vector for a storage kind.
 int vector_width(int precision);
 
-// One time step: src (post-collision, step n-1) -> dst (post-collision, step n).
+// Launch shape of the staged kernel.
+struct StagedPlan {
+    int stages = 2;          // shared-memory ring depth
+    int ctas_per_sm = 0;     // persistent CTAs per SM
+    int grid = 0;            // SMs x ctas_per_sm
+    int consumer_warps = 8;  // 4 or 8: tile width 32 x consumer_warps x V nodes
+    int hint = 0;            // L2 evict-first policy on the bulk loads
+};
+
+// Computes a staged plan on the current device (sets the kernel's shared
+// memory attribute; call outside stream capture).  stages <= 0 = default 2;
+// ctas_per_sm <= 0 = as many as fit; consumer_warps <= 0 = 8.
+cudaError_t staged_plan(int precision, int stages, int ctas_per_sm, int consumer_warps,
+                        int l2_hint, StagedPlan *out);
+int staged_tile_width(int precision, int consumer_warps);
+
+// One time step: src (post-collision, step n-1) -> dst (post-collision,
+// step n).  With rq non-null the launch also computes the residual sums of
+// the state at step n (5 doubles per block into rq->partials; *blocks_out
+// receives the block count).  `status` is a device word the staged kernel
+// sets when a bounded wait gives up.
 template <typename T>
 cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc_x, int bc_y,
-                        const Coef<typename Store<T>::C> &k, cudaStream_t stream);
+                        const Coef<typename Store<T>::C> &k, int *status,
+                        const ResidualReq<typename Store<T>::C> *rq, const StagedPlan &plan,
+                        int *blocks_out, cudaStream_t stream);
 
-// The bulk-copy staged variant (see staged.cu).  Returns
-// cudaErrorNotSupported when the lattice does not meet its layout rules.
+// Largest number of blocks a step launch of this kernel can have (sizes the
+// per-block residual partials).
+long long step_blocks(int kernel, int precision, int nx, int ny, const StagedPlan &plan);
+
+// The bulk-copy staged variant (see staged.cu).
 template <typename T>
 cudaError_t launch_step_staged(const T *src, T *dst, int nx, int ny, int bc_x, int bc_y,
-                               const Coef<typename Store<T>::C> &k, cudaStream_t stream);
-bool staged_supported(int precision, int nx, int ny);
+                               const Coef<typename Store<T>::C> &k, int *status,
+                               const ResidualReq<typename Store<T>::C> *rq,
+                               const StagedPlan &plan, int *blocks_out, cudaStream_t stream);
+bool staged_supported(int precision, int nx, int ny, int consumer_warps);
+
+// Fixed-order sum of per-block partials (5 doubles each) into sums[0..4].
+cudaError_t launch_finalize(const double *partials, int blocks, double *sums,
+                            cudaStream_t stream);
 
 // Read-out of the state at the current step.  `pulled` = the state is the
 // pull of the post-collision planes in `src` (step >= 1); otherwise `src`
@@ -48,17 +79,15 @@ cudaError_t launch_populations(const T *src, const Readout &r,
                                const Coef<typename Store<T>::C> &k, double *f,
                                cudaStream_t stream);
 
-// Residual pass: per node e, q of the state; accumulates in FP64
-//   sums[0] = sum (e - e_ref), sums[1] = sum (e - e_ref)^2,
-//   sums[2] = sum |q|^2, sums[3] = sum |(e,q) - prev|^2 (if have_prev),
-//   sums[4] = count of non-finite e or q,
-// and overwrites prev[3][n] with the current (e - e_ref, qx, qy).
-// `partials` holds RESIDUAL_BLOCKS*5 doubles of scratch.
+// Stand-alone residual pass over the state at the current step: the same
+// per-node sums as the fused step variant (residual_node in lbm_device.cuh),
+// 5 partial sums per block into `partials` (RESIDUAL_BLOCKS blocks), then
+// the fixed-order total into `sums`.
 constexpr int RESIDUAL_BLOCKS = 1216;    // 8 blocks per SM on 152 SMs
 template <typename T>
 cudaError_t launch_residual(const T *src, const Readout &r, const Coef<typename Store<T>::C> &k,
-                            double *prev, bool have_prev, double *partials, double *sums,
-                            cudaStream_t stream);
+                            typename Store<T>::C *prev, bool have_prev, double *partials,
+                            double *sums, cudaStream_t stream);
 
 // Initial state from device fields (Eq. 15): writes the state of step 0 into
 // `pre` and its collision into `post`.  qx/qy may be null.

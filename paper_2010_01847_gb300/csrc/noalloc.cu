@@ -89,9 +89,11 @@ __global__ void __launch_bounds__(256) total_sums(double *__restrict__ scratch, 
     }
 }
 
-// Failures are reported through lbm_last_error(NULL).
+// Failures are reported through lbm_last_error(NULL); a CUDA failure is
+// also cleared from the runtime's per-thread error record once reported.
 lbm_status noalloc_fail(lbm_status s, const char *msg) {
     plbm::set_global_error(msg);
+    if (s == LBM_ECUDA) (void)cudaGetLastError();
     return s;
 }
 

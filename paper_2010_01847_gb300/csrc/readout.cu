@@ -74,37 +74,11 @@ __global__ void populations_kernel(const T *__restrict__ src, Readout r,
     }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Block-wide sum of NV doubles per thread; result valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV]) {
-    __shared__ double sh[NV][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        const double w = warp_sum(v[q]);
-        if (lane == 0) sh[q][warp] = w;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            double w = lane < nw ? sh[q][lane] : 0.0;
-            v[q] = warp_sum(w);
-        }
-    }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256)
 residual_kernel(const T *__restrict__ src, Readout r, Coef<typename Store<T>::C> k,
-                double *__restrict__ prev, int have_prev, double *__restrict__ partials) {
+                typename Store<T>::C *__restrict__ prev, int have_prev,
+                double *__restrict__ partials) {
     using C = typename Store<T>::C;
     const long long n = (long long)r.nx * r.ny;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -113,25 +87,9 @@ residual_kernel(const T *__restrict__ src, Readout r, Coef<typename Store<T>::C>
         const int y = int(node / r.nx), x = int(node - (long long)y * r.nx);
         C d[8];
         state_node<T>(src, r, k, x, y, d);
-        double de, qx, qy;
-        node_moments_f64(d, r, de, qx, qy);
-        if (!(isfinite(de) && isfinite(qx) && isfinite(qy))) acc[4] += 1.0;
-        acc[0] += de;
-        acc[1] += de * de;
-        acc[2] += qx * qx + qy * qy;
-        if (have_prev) {
-            const double a = de - prev[node], b = qx - prev[n + node], c = qy - prev[2 * n + node];
-            acc[3] += a * a + b * b + c * c;
-        }
-        prev[node] = de;
-        prev[n + node] = qx;
-        prev[2 * n + node] = qy;
+        residual_node(d, k, (C)r.inv_scale, prev, n, node, have_prev != 0, acc);
     }
-    block_sum<5>(acc);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) partials[blockIdx.x * 5 + q] = acc[q];
-    }
+    block_sum5_store(acc, partials + (size_t)blockIdx.x * 5);
 }
 
 // Fixed-order sum of the per-block partials (deterministic result).
@@ -142,11 +100,7 @@ __global__ void __launch_bounds__(256) finalize_sums(const double *__restrict__ 
 #pragma unroll
         for (int q = 0; q < 5; ++q) acc[q] += partials[b * 5 + q];
     }
-    block_sum<5>(acc);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) sums[q] = acc[q];
-    }
+    block_sum5_store(acc, sums);
 }
 
 template <typename T>
@@ -223,13 +177,18 @@ cudaError_t launch_populations(const T *src, const Readout &r,
 
 template <typename T>
 cudaError_t launch_residual(const T *src, const Readout &r, const Coef<typename Store<T>::C> &k,
-                            double *prev, bool have_prev, double *partials, double *sums,
-                            cudaStream_t stream) {
+                            typename Store<T>::C *prev, bool have_prev, double *partials,
+                            double *sums, cudaStream_t stream) {
     residual_kernel<T><<<RESIDUAL_BLOCKS, 256, 0, stream>>>(src, r, k, prev, have_prev ? 1 : 0,
                                                             partials);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    finalize_sums<<<1, 256, 0, stream>>>(partials, RESIDUAL_BLOCKS, sums);
+    return launch_finalize(partials, RESIDUAL_BLOCKS, sums, stream);
+}
+
+cudaError_t launch_finalize(const double *partials, int blocks, double *sums,
+                            cudaStream_t stream) {
+    finalize_sums<<<1, 256, 0, stream>>>(partials, blocks, sums);
     return cudaGetLastError();
 }
 
@@ -258,7 +217,7 @@ cudaError_t launch_max_deviation(const double *e, const double *qx, const double
                                                const Coef<Store<T>::C> &, double *,           \
                                                cudaStream_t);                                 \
     template cudaError_t launch_residual<T>(const T *, const Readout &,                       \
-                                            const Coef<Store<T>::C> &, double *, bool,        \
+                                            const Coef<Store<T>::C> &, Store<T>::C *, bool,   \
                                             double *, double *, cudaStream_t);                \
     template cudaError_t launch_init<T>(const double *, const double *, const double *, int,  \
                                         int, double, double, const Coef<Store<T>::C> &, T *,  \

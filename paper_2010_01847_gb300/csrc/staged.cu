@@ -1,24 +1,460 @@
-// Bulk-copy staged stream-collide kernel (placeholder until implemented).
+// Staged stream-collide kernel: the bulk-copy engine (TMA) moves row
+// segments of all 8 planes into a ring of shared-memory stages while the
+// consumer warps collide the previous stage.
+//
+// Tile = one row segment of W = 32 CW V nodes (CW consumer warps, V =
+// 16 / sizeof(T)), i.e. 512 CW bytes per plane, plus one 16-byte halo vector
+// on each side.  Plane i of
+// output row y is pulled from row y - c_iy (Eq. 13, left-hand side), so the
+// producer copies, for each plane, that source row's segment
+// [x0 - V, x0 + W + V) (split at the x seam, where the halo wraps to the far
+// end of the row).  Every copy starts on a 16-byte boundary and is a multiple
+// of 16 bytes, as the bulk copy requires.
+//
+// Roles per CTA: warp CW lane 0 is the producer (waits until a stage is free,
+// arms the stage's "full" mbarrier with the byte count, issues
+// cp.async.bulk for the 8 plane segments); warps 0..CW-1 consume (wait "full",
+// pull from shared memory, seam/wall rules, collide, store 16-byte vectors
+// straight to global memory, release the stage on its "empty" mbarrier).
+// CTAs are persistent: tile t goes to CTA t mod gridDim.
+//
+// Every wait is bounded (iteration and clock limits).  A wait that gives up
+// sets bit 1 of *status and the role stops; the producer then waits (again
+// bounded) until every copy it issued has landed before the CTA can exit.
+#include <type_traits>
+
 #include "lbm_kernels.h"
 
 namespace plbm {
 
-bool staged_supported(int, int, int) { return false; }
+namespace {
 
-template <typename T>
-cudaError_t launch_step_staged(const T *, T *, int, int, int, int,
-                               const Coef<typename Store<T>::C> &, cudaStream_t) {
-    return cudaErrorNotSupported;
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+constexpr long long WAIT_ITERS = 1LL << 28;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-template cudaError_t launch_step_staged<float>(const float *, float *, int, int, int, int,
-                                               const Coef<float> &, cudaStream_t);
-template cudaError_t launch_step_staged<double>(const double *, double *, int, int, int, int,
-                                                const Coef<double> &, cudaStream_t);
-template cudaError_t launch_step_staged<__half>(const __half *, __half *, int, int, int, int,
-                                                const Coef<float> &, cudaStream_t);
-template cudaError_t launch_step_staged<__nv_bfloat16>(const __nv_bfloat16 *, __nv_bfloat16 *,
-                                                       int, int, int, int, const Coef<float> &,
-                                                       cudaStream_t);
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (long long it = 0; it < WAIT_ITERS; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255) == 255 && clock64() - t0 > WAIT_CYCLES) break;
+    }
+    atomicOr(status, 1);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy completing on an mbarrier (the TMA engine).
+// With `hinted`, the copy carries an L2 evict-first policy (the data is read
+// exactly once per step).
+__device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src, uint32_t bytes,
+                                          uint64_t *bar, bool hinted, uint64_t policy) {
+    if (hinted)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+            "[%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst_smem)),
+            "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+            : "memory");
+    else
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(smem_addr(dst_smem)),
+            "l"(src), "r"(bytes), "r"(smem_addr(bar))
+            : "memory");
+}
+
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void st_stream(void *p, uint4 v) {
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    static constexpr int V = 4;
+    __device__ static void unpack(uint4 r, float (&o)[4]) {
+        o[0] = __uint_as_float(r.x); o[1] = __uint_as_float(r.y);
+        o[2] = __uint_as_float(r.z); o[3] = __uint_as_float(r.w);
+    }
+    __device__ static uint4 pack(const float (&o)[4]) {
+        return make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]),
+                          __float_as_uint(o[3]));
+    }
+};
+template <> struct Vec16<double> {
+    static constexpr int V = 2;
+    __device__ static void unpack(uint4 r, double (&o)[2]) {
+        o[0] = __hiloint2double((int)r.y, (int)r.x);
+        o[1] = __hiloint2double((int)r.w, (int)r.z);
+    }
+    __device__ static uint4 pack(const double (&o)[2]) {
+        return make_uint4((unsigned)__double2loint(o[0]), (unsigned)__double2hiint(o[0]),
+                          (unsigned)__double2loint(o[1]), (unsigned)__double2hiint(o[1]));
+    }
+};
+template <> struct Vec16<__half> {
+    static constexpr int V = 8;
+    __device__ static void unpack(uint4 r, float (&o)[8]) {
+        const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[j]));
+            o[2 * j] = f.x;
+            o[2 * j + 1] = f.y;
+        }
+    }
+    __device__ static uint4 pack(const float (&o)[8]) {
+        unsigned w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __half2 h = __floats2half2_rn(o[2 * j], o[2 * j + 1]);
+            w[j] = *reinterpret_cast<const unsigned *>(&h);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+template <> struct Vec16<__nv_bfloat16> {
+    static constexpr int V = 8;
+    __device__ static void unpack(uint4 r, float (&o)[8]) {
+        const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[j]));
+            o[2 * j] = f.x;
+            o[2 * j + 1] = f.y;
+        }
+    }
+    __device__ static uint4 pack(const float (&o)[8]) {
+        unsigned w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
+            w[j] = *reinterpret_cast<const unsigned *>(&h);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+
+template <typename T, int CW> constexpr int tile_width() { return CW * 32 * Vec16<T>::V; }
+template <typename T, int CW> constexpr int row_len() {
+    return tile_width<T, CW>() + 2 * Vec16<T>::V;
+}
+template <typename T, int CW> constexpr int stage_bytes() {
+    return 8 * row_len<T, CW>() * (int)sizeof(T);
+}
+
+// 16-bit storage keeps 8 nodes per consumer thread; asking for two CTAs per
+// SM caps its registers so two rings fit on an SM.
+template <typename T, int CW, bool RES>
+__global__ void __launch_bounds__((CW + 1) * 32, (sizeof(T) == 2 ? 2 : 1))
+step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long long plane,
+            int bc_x, int bc_y, int stages, int hinted, Coef<typename Store<T>::C> k,
+            int *status, ResidualReq<typename Store<T>::C> rq) {
+    using C = typename Store<T>::C;
+    constexpr int V = Vec16<T>::V;
+    constexpr int W = tile_width<T, CW>();
+    constexpr int RL = row_len<T, CW>();
+    constexpr int SB = stage_bytes<T, CW>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *ring = reinterpret_cast<T *>(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)stages * SB);
+    uint64_t *empty = full + stages;
+
+    const int tiles_per_row = nx / W;
+    const long long n_tiles = (long long)tiles_per_row * ny;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+
+    if (warp == CW) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            const uint64_t policy = hinted ? evict_first_policy() : 0ull;
+            long long issued = 0;
+            for (long long tile = blockIdx.x, kk = 0; tile < n_tiles;
+                 tile += gridDim.x, ++kk) {
+                const int s = (int)(kk % stages);
+                const uint32_t ph = (uint32_t)((kk / stages) & 1);
+                if (!mbar_wait(&empty[s], ph ^ 1u, status)) break;
+                const int y = (int)(tile / tiles_per_row);
+                const int x0 = (int)(tile - (long long)y * tiles_per_row) * W;
+                mbar_expect_tx(&full[s], (uint32_t)SB);
+                T *stage = ring + (size_t)s * 8 * RL;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    int sy = y - cy_of(i);
+                    sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+                    const T *row = src + (long long)i * plane + (long long)sy * nx;
+                    T *d = stage + i * RL;
+                    if (x0 > 0 && x0 + W < nx) {
+                        bulk_copy(d, row + x0 - V, RL * sizeof(T), &full[s], hinted, policy);
+                    } else {
+                        bulk_copy(d, row + (x0 == 0 ? nx - V : x0 - V), V * sizeof(T), &full[s],
+                                  hinted, policy);
+                        bulk_copy(d + V, row + x0, W * sizeof(T), &full[s], hinted, policy);
+                        bulk_copy(d + V + W, row + (x0 + W == nx ? 0 : x0 + W), V * sizeof(T),
+                                  &full[s], hinted, policy);
+                    }
+                }
+                issued = kk + 1;
+            }
+            // every copy issued must land before the CTA may exit
+            for (long long kk = issued > stages ? issued - stages : 0; kk < issued; ++kk)
+                mbar_wait(&full[kk % stages], (uint32_t)((kk / stages) & 1), status);
+        }
+    } else {
+        // ---------------- consumers ----------------
+        const int t = threadIdx.x;          // owns nodes x0 + t V .. + V - 1
+        const bool walls = bc_y == BC_WALLS;
+        for (long long tile = blockIdx.x, kk = 0; tile < n_tiles; tile += gridDim.x, ++kk) {
+            const int s = (int)(kk % stages);
+            const uint32_t ph = (uint32_t)((kk / stages) & 1);
+            if (!mbar_wait(&full[s], ph, status)) break;
+            const int y = (int)(tile / tiles_per_row);
+            const int x0 = (int)(tile - (long long)y * tiles_per_row) * W;
+            const T *stage = ring + (size_t)s * 8 * RL;
+            C d[8][V];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const T *r = stage + i * RL + V + t * V;
+                Vec16<T>::unpack(*reinterpret_cast<const uint4 *>(r), d[i]);
+                const int cx = cx_of(i);
+                if (cx > 0) {
+                    C left = Store<T>::load(r[-1]);
+                    if (bc_x == BC_GRADIENT && x0 == 0 && t == 0)
+                        left += (i < 4) ? k.jump_axis : k.jump_diag;     // Eq. 59
+#pragma unroll
+                    for (int j = V - 1; j >= 1; --j) d[i][j] = d[i][j - 1];
+                    d[i][0] = left;
+                } else if (cx < 0) {
+                    C right = Store<T>::load(r[V]);
+                    if (bc_x == BC_GRADIENT && x0 + W == nx && t == CW * 32 - 1)
+                        right -= (i < 4) ? k.jump_axis : k.jump_diag;    // Eq. 60
+#pragma unroll
+                    for (int j = 0; j < V - 1; ++j) d[i][j] = d[i][j + 1];
+                    d[i][V - 1] = right;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);     // this warp is done with the stage
+
+            const bool bottom = walls && y == 0;
+            const bool top = walls && y == ny - 1;
+            const long long out = (long long)y * nx + x0 + t * V;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                C n[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) n[i] = d[i][j];
+                if (bottom) wall_bottom(n, k);
+                if (top) wall_top(n, k);
+                if (RES) residual_node(n, k, rq.inv_scale, rq.prev, plane, out + j,
+                                       rq.have_prev != 0, acc);
+                collide(n, k);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) d[i][j] = n[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                st_stream(dst + (long long)i * plane + out, Vec16<T>::pack(d[i]));
+        }
+    }
+    if (RES) {
+        __syncthreads();
+        block_sum5_store(acc, rq.partials + (size_t)blockIdx.x * 5);
+    }
+}
+
+constexpr int MAX_STAGES = 6;
+
+template <typename T, int CW>
+constexpr size_t smem_bytes(int stages) {
+    return (size_t)stages * stage_bytes<T, CW>() + 2 * (size_t)stages * sizeof(uint64_t);
+}
+
+template <typename T> constexpr int prec_of() {
+    return sizeof(T) == 4 ? PREC_FP32 : sizeof(T) == 8 ? PREC_FP64
+           : (std::is_same<T, __half>::value ? PREC_FP16 : PREC_BF16);
+}
+
+template <typename T, int CW, bool RES> constexpr auto kernel_of() {
+    return step_staged<T, CW, RES>;
+}
+
+struct DeviceInfo {
+    int sms = 0;
+    bool prepared[4][2] = {};   // per storage kind, per consumer-warp variant
+};
+DeviceInfo g_info[64];
+
+// Once per device, storage kind and variant: allow the kernel's largest ring.
+template <typename T, int CW>
+cudaError_t prepare(int dev) {
+    DeviceInfo &info = g_info[dev];
+    if (!info.sms) {
+        cudaError_t e = cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    const int vi = CW == 8 ? 0 : 1;
+    if (!info.prepared[prec_of<T>()][vi]) {
+        int optin = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        const int want = (int)smem_bytes<T, CW>(MAX_STAGES) + 2048;
+        const int limit = want < optin ? want : optin;
+        e = cudaFuncSetAttribute(kernel_of<T, CW, false>(),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kernel_of<T, CW, true>(),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+        if (e != cudaSuccess) return e;
+        info.prepared[prec_of<T>()][vi] = true;
+    }
+    return cudaSuccess;
+}
+
+template <typename T, int CW>
+cudaError_t plan_for(int stages, int ctas_per_sm, int hint, StagedPlan *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (stages < 2 || stages > MAX_STAGES) return cudaErrorInvalidValue;
+    if ((e = prepare<T, CW>(dev)) != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_of<T, CW, false>(),
+                                                      (CW + 1) * 32, smem_bytes<T, CW>(stages));
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    out->stages = stages;
+    out->ctas_per_sm = per_sm;
+    out->grid = g_info[dev].sms * per_sm;
+    out->consumer_warps = CW;
+    out->hint = hint ? 1 : 0;
+    return cudaSuccess;
+}
+
+template <typename T, int CW>
+cudaError_t launch_cw(const T *src, T *dst, int nx, int ny, int bc_x, int bc_y,
+                      const Coef<typename Store<T>::C> &k, int *status,
+                      const ResidualReq<typename Store<T>::C> *rq, const StagedPlan &plan,
+                      int *blocks_out, cudaStream_t stream) {
+    const long long plane = (long long)nx * ny;
+    const long long n_tiles = (long long)(nx / tile_width<T, CW>()) * ny;
+    const int grid = (int)(n_tiles < plan.grid ? n_tiles : plan.grid);
+    const size_t smem = smem_bytes<T, CW>(plan.stages);
+    if (blocks_out) *blocks_out = grid;
+    if (rq) {
+        step_staged<T, CW, true><<<grid, (CW + 1) * 32, smem, stream>>>(
+            src, dst, nx, ny, plane, bc_x, bc_y, plan.stages, plan.hint, k, status, *rq);
+    } else {
+        ResidualReq<typename Store<T>::C> none{};
+        step_staged<T, CW, false><<<grid, (CW + 1) * 32, smem, stream>>>(
+            src, dst, nx, ny, plane, bc_x, bc_y, plan.stages, plan.hint, k, status, none);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t plan_t(int stages, int ctas_per_sm, int cw, int hint, StagedPlan *out) {
+    return cw == 4 ? plan_for<T, 4>(stages, ctas_per_sm, hint, out)
+                   : plan_for<T, 8>(stages, ctas_per_sm, hint, out);
+}
+
+}  // namespace
+
+int staged_tile_width(int precision, int consumer_warps) {
+    const int v = precision == PREC_FP32 ? 4 : precision == PREC_FP64 ? 2 : 8;
+    return consumer_warps * 32 * v;
+}
+
+bool staged_supported(int precision, int nx, int ny, int consumer_warps) {
+    if (consumer_warps != 4 && consumer_warps != 8) return false;
+    const int w = staged_tile_width(precision, consumer_warps);
+    return ny >= 1 && nx >= w && nx % w == 0;
+}
+
+cudaError_t staged_plan(int precision, int stages, int ctas_per_sm, int consumer_warps,
+                        int l2_hint, StagedPlan *out) {
+    if (stages <= 0) stages = 2;
+    if (consumer_warps <= 0) consumer_warps = 8;
+    if (consumer_warps != 4 && consumer_warps != 8) return cudaErrorInvalidValue;
+    switch (precision) {
+        case PREC_FP32: return plan_t<float>(stages, ctas_per_sm, consumer_warps, l2_hint, out);
+        case PREC_FP64: return plan_t<double>(stages, ctas_per_sm, consumer_warps, l2_hint, out);
+        case PREC_FP16: return plan_t<__half>(stages, ctas_per_sm, consumer_warps, l2_hint, out);
+        default:
+            return plan_t<__nv_bfloat16>(stages, ctas_per_sm, consumer_warps, l2_hint, out);
+    }
+}
+
+template <typename T>
+cudaError_t launch_step_staged(const T *src, T *dst, int nx, int ny, int bc_x, int bc_y,
+                               const Coef<typename Store<T>::C> &k, int *status,
+                               const ResidualReq<typename Store<T>::C> *rq,
+                               const StagedPlan &plan, int *blocks_out, cudaStream_t stream) {
+    if (plan.consumer_warps == 4)
+        return launch_cw<T, 4>(src, dst, nx, ny, bc_x, bc_y, k, status, rq, plan, blocks_out,
+                               stream);
+    return launch_cw<T, 8>(src, dst, nx, ny, bc_x, bc_y, k, status, rq, plan, blocks_out, stream);
+}
+
+#define PLBM_STAGED(T)                                                                       \
+    template cudaError_t launch_step_staged<T>(const T *, T *, int, int, int, int,           \
+                                               const Coef<Store<T>::C> &, int *,             \
+                                               const ResidualReq<Store<T>::C> *,             \
+                                               const StagedPlan &, int *, cudaStream_t);
+PLBM_STAGED(float)
+PLBM_STAGED(double)
+PLBM_STAGED(__half)
+PLBM_STAGED(__nv_bfloat16)
 
 }  // namespace plbm

@@ -1,11 +1,13 @@
 // Fused pull-stream + boundary + collision kernels: one launch is one time
 // step of Eq. 13 over the whole lattice.
 //
-// Both kernels read the post-collision planes of step n-1 (`src`), pull the
+// The kernels read the post-collision planes of step n-1 (`src`), pull the
 // populations arriving at each node (left-hand side of Eq. 13, seam jump of
 // Eqs. 59-60, diffuse walls of Eq. 58), collide them in registers
 // (Eqs. 15, 16, 53, 54) and write the post-collision planes of step n
 // (`dst`).  Layout: structure of arrays, 8 planes of ny*nx, x fastest.
+// With RES the kernel also accumulates the residual sums of the pulled state
+// (the state at step n) and writes one set of 5 partial sums per block.
 #include "lbm_kernels.h"
 
 namespace plbm {
@@ -13,20 +15,25 @@ namespace plbm {
 // ---------------------------------------------------------------------------
 // Scalar kernel: one thread per node, any nx.  Serves ragged lattices (nx not
 // a multiple of the vector width) and is the simplest statement of the step.
-template <typename T>
+template <typename T, bool RES>
 __global__ void __launch_bounds__(256)
 step_scalar(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
-            long long plane, int bc_x, int bc_y, Coef<typename Store<T>::C> k) {
+            long long plane, int bc_x, int bc_y, Coef<typename Store<T>::C> k,
+            ResidualReq<typename Store<T>::C> rq) {
     using C = typename Store<T>::C;
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= plane) return;
-    const int y = int(node / nx);
-    const int x = int(node - (long long)y * nx);
-    C d[8];
-    pull_node<T>(src, plane, nx, ny, x, y, bc_x, bc_y, k, d);
-    collide(d, k);
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (node < plane) {
+        const int y = int(node / nx);
+        const int x = int(node - (long long)y * nx);
+        C d[8];
+        pull_node<T>(src, plane, nx, ny, x, y, bc_x, bc_y, k, d);
+        if (RES) residual_node(d, k, rq.inv_scale, rq.prev, plane, node, rq.have_prev != 0, acc);
+        collide(d, k);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) dst[(long long)i * plane + node] = Store<T>::put(d[i]);
+        for (int i = 0; i < 8; ++i) dst[(long long)i * plane + node] = Store<T>::put(d[i]);
+    }
+    if (RES) block_sum5_store(acc, rq.partials + (size_t)blockIdx.x * 5);
 }
 
 // ---------------------------------------------------------------------------
@@ -115,10 +122,11 @@ __device__ __forceinline__ void st_stream(void *p, uint4 v) {
 // rows' ends, load that one element directly (wrapping at the seam).
 // Requires nx % V == 0.  Threads are laid out row-major over the lattice,
 // so a warp may straddle two rows; the row test handles that.
-template <typename T>
+template <typename T, bool RES>
 __global__ void __launch_bounds__(256)
 step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
-            long long plane, int bc_x, int bc_y, Coef<typename Store<T>::C> k) {
+            long long plane, int bc_x, int bc_y, Coef<typename Store<T>::C> k,
+            ResidualReq<typename Store<T>::C> rq) {
     using C = typename Store<T>::C;
     constexpr int V = Pack<T>::V;
     const int tpr = nx / V;
@@ -186,40 +194,67 @@ step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
             d[i][V - 1] = right;
         }
     }
-    if (!active) return;
 
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (active) {
+        const long long out = (long long)y * nx + x0;
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-        C n[8];
+        for (int j = 0; j < V; ++j) {
+            C n[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) n[i] = d[i][j];
-        if (bottom) wall_bottom(n, k);
-        if (top) wall_top(n, k);
-        collide(n, k);
+            for (int i = 0; i < 8; ++i) n[i] = d[i][j];
+            if (bottom) wall_bottom(n, k);
+            if (top) wall_top(n, k);
+            if (RES) residual_node(n, k, rq.inv_scale, rq.prev, plane, out + j,
+                                   rq.have_prev != 0, acc);
+            collide(n, k);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) d[i][j] = n[i];
+            for (int i = 0; i < 8; ++i) d[i][j] = n[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            st_stream(dst + (long long)i * plane + out, Pack<T>::pack(d[i]));
     }
-    const long long out = (long long)y * nx + x0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, Pack<T>::pack(d[i]));
+    if (RES) block_sum5_store(acc, rq.partials + (size_t)blockIdx.x * 5);
 }
 
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc_x, int bc_y,
-                        const Coef<typename Store<T>::C> &k, cudaStream_t stream) {
+                        const Coef<typename Store<T>::C> &k, int *status,
+                        const ResidualReq<typename Store<T>::C> *rq, const StagedPlan &plan,
+                        int *blocks_out, cudaStream_t stream) {
     const long long plane = (long long)nx * ny;
+    if (kernel == KERNEL_STAGED)
+        return launch_step_staged<T>(src, dst, nx, ny, bc_x, bc_y, k, status, rq, plan,
+                                     blocks_out, stream);
+    const ResidualReq<typename Store<T>::C> none{};
+    const long long threads = kernel == KERNEL_VECTOR ? plane / Pack<T>::V : plane;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (blocks_out) *blocks_out = (int)blocks;
     if (kernel == KERNEL_VECTOR) {
-        const long long threads = plane / Pack<T>::V;
-        const unsigned blocks = (unsigned)((threads + 255) / 256);
-        step_vector<T><<<blocks, 256, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y, k);
-    } else if (kernel == KERNEL_STAGED) {
-        return launch_step_staged<T>(src, dst, nx, ny, bc_x, bc_y, k, stream);
+        if (rq)
+            step_vector<T, true><<<blocks, 256, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
+                                                             k, *rq);
+        else
+            step_vector<T, false><<<blocks, 256, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                              bc_y, k, none);
     } else {
-        const unsigned blocks = (unsigned)((plane + 255) / 256);
-        step_scalar<T><<<blocks, 256, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y, k);
+        if (rq)
+            step_scalar<T, true><<<blocks, 256, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
+                                                             k, *rq);
+        else
+            step_scalar<T, false><<<blocks, 256, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                              bc_y, k, none);
     }
     return cudaGetLastError();
+}
+
+long long step_blocks(int kernel, int precision, int nx, int ny, const StagedPlan &plan) {
+    const long long plane = (long long)nx * ny;
+    if (kernel == KERNEL_STAGED) return plan.grid;
+    const long long threads = kernel == KERNEL_VECTOR ? plane / vector_width(precision) : plane;
+    return (threads + 255) / 256;
 }
 
 int vector_width(int precision) {
@@ -230,14 +265,14 @@ int vector_width(int precision) {
     }
 }
 
-template cudaError_t launch_step<float>(int, const float *, float *, int, int, int, int,
-                                        const Coef<float> &, cudaStream_t);
-template cudaError_t launch_step<double>(int, const double *, double *, int, int, int, int,
-                                         const Coef<double> &, cudaStream_t);
-template cudaError_t launch_step<__half>(int, const __half *, __half *, int, int, int, int,
-                                         const Coef<float> &, cudaStream_t);
-template cudaError_t launch_step<__nv_bfloat16>(int, const __nv_bfloat16 *, __nv_bfloat16 *,
-                                                int, int, int, int, const Coef<float> &,
-                                                cudaStream_t);
+#define PLBM_STEP(T)                                                                         \
+    template cudaError_t launch_step<T>(int, const T *, T *, int, int, int, int,             \
+                                        const Coef<Store<T>::C> &, int *,                    \
+                                        const ResidualReq<Store<T>::C> *, const StagedPlan &, \
+                                        int *, cudaStream_t);
+PLBM_STEP(float)
+PLBM_STEP(double)
+PLBM_STEP(__half)
+PLBM_STEP(__nv_bfloat16)
 
 }  // namespace plbm

@@ -41,17 +41,30 @@ LATTICES = [
     (8, 2, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3),      # two wall rows only
     (1, 1, plbm.PERIODIC, plbm.PERIODIC, 0.0),
     (16, 1, plbm.PERIODIC_GRADIENT, plbm.PERIODIC, 1e-3),
+    # widths the staged kernel takes (tiles of 4 KiB per plane row)
+    (2048, 24, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3),
+    (4096, 9, plbm.PERIODIC_GRADIENT, plbm.PERIODIC, -1e-3),
+    (1024, 2, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3),
 ]
+VEC = {"fp32": 4, "fp64": 2, "fp16": 8, "bf16": 8}
+
+
+def _kernel_ok(kernel, nx, precision):
+    v = VEC[precision]
+    if kernel == "vector":
+        return nx % v == 0
+    if kernel == "staged":
+        return nx % (256 * v) == 0
+    return True
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16", "bf16"])
-@pytest.mark.parametrize("kernel", ["scalar", "vector", "auto"])
+@pytest.mark.parametrize("kernel", ["scalar", "vector", "staged", "auto"])
 @pytest.mark.parametrize("lattice", LATTICES, ids=lambda l: f"{l[0]}x{l[1]}_bc{l[2]}{l[3]}")
 def test_parity_small(lattice, kernel, precision):
     nx, ny, bcx, bcy, de = lattice
-    vec = {"fp32": 4, "fp64": 2, "fp16": 8, "bf16": 8}[precision]
-    if kernel == "vector" and nx % vec:
-        pytest.skip("vector kernel needs nx % V == 0")
+    if not _kernel_ok(kernel, nx, precision):
+        pytest.skip(f"{kernel} kernel cannot take nx={nx} in {precision}")
     tau_N, tau_R = 0.9, 15.0
     fields = inputs.random_state_fields(nx, ny, seed=nx * 1000 + ny)
     steps = 57
@@ -93,13 +106,54 @@ def test_parity_degenerate_relaxation(tau_N, tau_R):
     assert err_e <= TOL["fp32"] and err_q <= TOL["fp32"], (err_e, err_q)
 
 
-def test_kernels_and_graph_chunks_agree_bitwise():
-    nx, ny = 512, 64
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "fp64"])
+@pytest.mark.parametrize("shape", [(2, 0, 4, 0), (3, 1, 8, 1), (6, 0, 4, 1), (2, 2, 8, 0)])
+def test_staged_shapes_agree_bitwise(precision, shape):
+    """Every staged launch shape (ring depth, CTAs/SM, consumer warps, L2
+    hint) gives the vector kernel's populations bit for bit."""
+    nx, ny = 2048, 19
+    fields = inputs.random_state_fields(nx, ny, seed=41)
+    bc = (plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3)
+    ref = gpu_run(nx, ny, 0.85, 7.0, fields, 33, *bc, precision, "vector")
+    g = plbm.Lattice(nx, ny, 0.85, 7.0, *bc, precision=precision, kernel="staged")
+    g.set_staged_config(*shape)
+    cfg = g.staged_config
+    assert cfg["stages"] == shape[0] and cfg["consumer_warps"] == shape[2]
+    g.init(*fields)
+    g.step(33)
+    assert np.array_equal(ref.populations(), g.populations())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_autotune_keeps_state_and_results(precision):
+    nx, ny = 2048, 17
+    fields = inputs.random_state_fields(nx, ny, seed=13)
+    bc = (plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3)
+    ref = gpu_run(nx, ny, 0.8, 9.0, fields, 40, *bc, precision, "vector")
+    g = gpu_run(nx, ny, 0.8, 9.0, fields, 15, *bc, precision, "scalar")
+    before = g.populations()
+    kernel, us = g.autotune(8)
+    assert kernel in ("vector", "staged") and us > 0
+    assert g.step_count == 15 and g.kernel == kernel
+    assert np.array_equal(before, g.populations())
+    g.step(25)
+    assert np.array_equal(ref.populations(), g.populations())
+    fresh = plbm.Lattice(nx, ny, 0.8, 9.0, *bc, precision=precision)
+    fresh.autotune(4)                      # before lbm_init: no state to keep
+    fresh.init(*fields)
+    fresh.step(40)
+    assert np.array_equal(ref.populations(), fresh.populations())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_kernels_and_graph_chunks_agree_bitwise(precision):
+    nx, ny = 2048, 40
     fields = inputs.random_state_fields(nx, ny, seed=5)
     outs = []
-    for kernel, chunk in [("scalar", 0), ("vector", 0), ("vector", 64), ("auto", 16)]:
+    for kernel, chunk in [("scalar", 0), ("vector", 0), ("vector", 64), ("staged", 0),
+                          ("staged", 64), ("auto", 16)]:
         g = gpu_run(nx, ny, 0.8, 9.0, fields, 150, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS,
-                    1e-3, "fp32", kernel, graph_chunk=chunk)
+                    1e-3, precision, kernel, graph_chunk=chunk)
         outs.append(g.populations())
     for o in outs[1:]:
         assert np.array_equal(outs[0], o)
@@ -220,6 +274,28 @@ def test_residual_matches_oracle_definition():
     den = math.sqrt(((b[0] - b[0].mean()) ** 2).sum() + (b[1] ** 2).sum() + (b[2] ** 2).sum())
     assert r1 == pytest.approx(num / (K * den), rel=1e-9)
     assert en1 == pytest.approx(b[0].sum(), rel=1e-13)
+
+
+@pytest.mark.parametrize("kernel", ["scalar", "vector", "staged"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16"])
+def test_fused_step_residual_matches_separate_pass(kernel, precision):
+    """lbm_step_residual == lbm_step + lbm_residual: same r, energy and state."""
+    nx, ny = 2048, 20
+    fields = inputs.random_state_fields(nx, ny, seed=31)
+    bc = (plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3)
+    a = gpu_run(nx, ny, 0.9, 11.0, fields, 0, *bc, precision, kernel)
+    b = gpu_run(nx, ny, 0.9, 11.0, fields, 0, *bc, precision, kernel)
+    ra0, ea0 = a.residual()
+    rb0, eb0 = b.step_residual(0)
+    assert math.isinf(ra0) and math.isinf(rb0) and ea0 == eb0
+    for k in (7, 30, 1):
+        a.step(k)
+        ra, ea = a.residual()
+        rb, eb = b.step_residual(k)
+        assert rb == pytest.approx(ra, rel=1e-12)
+        assert eb == pytest.approx(ea, rel=1e-14)
+    assert a.step_count == b.step_count
+    assert np.array_equal(a.populations(), b.populations())
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16", "fp64"])
