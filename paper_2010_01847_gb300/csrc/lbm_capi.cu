@@ -222,7 +222,8 @@ lbm_status ensure_scratch(lbm_ctx *c, bool need_prev) {
     }
     if (need_prev) {
         long long blocks = step_blocks(c->kernel, c->precision, c->nx, c->ny, c->plan);
-        if (blocks < RESIDUAL_BLOCKS) blocks = RESIDUAL_BLOCKS;
+        const long long rb = readout_blocks(c->precision, c->nx, c->ny);
+        if (blocks < rb) blocks = rb;
         if (blocks > c->partial_blocks) {
             cudaFree(c->partials);
             c->partials = nullptr;

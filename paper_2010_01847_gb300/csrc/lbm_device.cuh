@@ -147,37 +147,65 @@ __device__ __forceinline__ void pull_node(const T *__restrict__ src, long long p
 }
 
 // Residual contribution of one node of the state at step n (pulled, after
-// the boundary, before collision).  de = e - e_ref and q are formed in the
-// compute type C; each node's terms are added to the FP64 accumulators acc,
-// and compared with / written to the history planes prev (3 planes of C:
-// de, qx, qy at the previous residual):
-//   acc[0] += de, acc[1] += de^2, acc[2] += |q|^2,
-//   acc[3] += |(de, q) - prev|^2, acc[4] += 1 if a value is not finite.
-// Every kernel that reduces a residual uses this function, so the per-node
-// terms are bit-identical between them; only the FP64 summation order
-// differs.
+// the boundary, before collision), in the compute type C.  de = e - e_ref and
+// q are added to the thread's partial sums loc (in node order) and compared
+// with / replace the node's history values (de, qx, qy at the previous
+// residual) held in h_de, h_qx, h_qy:
+//   loc[0] += de, loc[1] += de^2, loc[2] += |q|^2,
+//   loc[3] += |(de, q) - history|^2, loc[4] += 1 if a value is not finite.
+// warp_flush_residual then sums loc over the warp in C (a fixed shuffle
+// order) and adds the warp's sums to FP64 accumulators.  FP64 arithmetic
+// runs at a small fraction of the FP32 rate on this GPU, so it is kept to
+// one conversion and add per warp and quantity.
 template <typename C>
-__device__ __forceinline__ void residual_node(const C (&d)[8], const Coef<C> &k, C inv_s,
-                                              C *__restrict__ prev, long long n,
-                                              long long node, bool have_prev,
-                                              double (&acc)[5]) {
+__device__ __forceinline__ void residual_terms(const C (&d)[8], const Coef<C> &k, C inv_s,
+                                               C &h_de, C &h_qx, C &h_qy, bool have_prev,
+                                               C (&loc)[5]) {
     const C rho = ((d[0] + d[2]) + (d[1] + d[3])) + ((d[4] + d[6]) + (d[5] + d[7]));
     const C mx = (d[0] - d[2]) + (d[4] - d[6]) + (d[7] - d[5]);
     const C my = (d[1] - d[3]) + (d[4] - d[6]) + (d[5] - d[7]);
     const C de = rho * inv_s;
     const C qx = (mx - k.lambda * mx) * inv_s;
     const C qy = (my - k.lambda * my) * inv_s;
-    if (!(isfinite(de) && isfinite(qx) && isfinite(qy))) acc[4] += 1.0;
-    acc[0] += (double)de;
-    acc[1] += (double)(de * de);
-    acc[2] += (double)(qx * qx + qy * qy);
+    if (!(isfinite(de) && isfinite(qx) && isfinite(qy))) loc[4] += C(1);
+    loc[0] += de;
+    loc[1] += de * de;
+    loc[2] += qx * qx + qy * qy;
     if (have_prev) {
-        const C a = de - prev[node], b = qx - prev[n + node], c = qy - prev[2 * n + node];
-        acc[3] += (double)(a * a + b * b + c * c);
+        const C a = de - h_de, b = qx - h_qx, c = qy - h_qy;
+        loc[3] += a * a + b * b + c * c;
     }
-    prev[node] = de;
-    prev[n + node] = qx;
-    prev[2 * n + node] = qy;
+    h_de = de;
+    h_qx = qx;
+    h_qy = qy;
+}
+
+// Same for one node whose history lives in the planes prev (3 x n of C).
+template <typename C>
+__device__ __forceinline__ void residual_node(const C (&d)[8], const Coef<C> &k, C inv_s,
+                                              C *__restrict__ prev, long long n,
+                                              long long node, bool have_prev, C (&loc)[5]) {
+    C h0 = have_prev ? prev[node] : C(0);
+    C h1 = have_prev ? prev[n + node] : C(0);
+    C h2 = have_prev ? prev[2 * n + node] : C(0);
+    residual_terms(d, k, inv_s, h0, h1, h2, have_prev, loc);
+    prev[node] = h0;
+    prev[n + node] = h1;
+    prev[2 * n + node] = h2;
+}
+
+// Sums loc over the (full) warp in C, adds the totals to acc in lane 0 and
+// clears loc.  Every lane of the warp must call it.
+template <typename C>
+__device__ __forceinline__ void warp_flush_residual(C (&loc)[5], double (&acc)[5]) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        C v = loc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) acc[q] += (double)v;
+        loc[q] = C(0);
+    }
 }
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
@@ -203,6 +231,28 @@ __device__ __forceinline__ void block_sum5_store(const double (&v)[5], double *o
         for (int q = 0; q < 5; ++q) {
             const double w = warp_sum_f64(lane < nw ? sh[q][lane] : 0.0);
             if (lane == 0) out[q] = w;
+        }
+    }
+}
+
+// Block-wide sum when only lane 0 of each warp holds values (after
+// warp_flush_residual): no FP64 shuffles; thread 0 adds the warps' values in
+// warp order and writes out[0..4].  Every thread must call it.
+__device__ __forceinline__ void block_sum5_lane0(const double (&v)[5], double *out) {
+    __shared__ double sh[5][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) sh[q][warp] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[q][w];
+            out[q] = s;
         }
     }
 }

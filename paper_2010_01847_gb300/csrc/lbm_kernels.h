@@ -47,13 +47,16 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
 // per-block residual partials).
 long long step_blocks(int kernel, int precision, int nx, int ny, const StagedPlan &plan);
 
-// The bulk-copy staged variant (see staged.cu).
+// The bulk-copy staged variant (see staged.cu); plain steps only (a step
+// with the fused residual runs on the vector kernel).
 template <typename T>
 cudaError_t launch_step_staged(const T *src, T *dst, int nx, int ny, int bc_x, int bc_y,
                                const Coef<typename Store<T>::C> &k, int *status,
-                               const ResidualReq<typename Store<T>::C> *rq,
                                const StagedPlan &plan, int *blocks_out, cudaStream_t stream);
 bool staged_supported(int precision, int nx, int ny, int consumer_warps);
+
+// Blocks of the stand-alone residual pass (sizes its per-block partials).
+long long readout_blocks(int precision, int nx, int ny);
 
 // Fixed-order sum of per-block partials (5 doubles each) into sums[0..4].
 cudaError_t launch_finalize(const double *partials, int blocks, double *sums,

@@ -1,7 +1,10 @@
-// Initialisation and read-out kernels: Eq. 15 initial state, moments
-// (Eqs. 53-54), raw populations, and the FP64 residual / energy reduction.
-// None of these is on the per-step path; they run once per read-out.
+// Initialisation and read-out kernels: the Eq. 15 initial state, moments
+// (Eqs. 53-54), raw populations, and the residual / energy reduction.  None
+// is on the per-step path.  Per-node arithmetic runs in the compute type C
+// (FP64 arithmetic is slow on this GPU); only the FP64 outputs and the
+// per-warp sums of the reduction are formed in double.
 #include "lbm_kernels.h"
+#include "vector_pull.cuh"
 
 namespace plbm {
 
@@ -21,37 +24,109 @@ __device__ __forceinline__ void state_node(const T *__restrict__ src, const Read
     }
 }
 
-// e - e_ref, qx, qy of one node in FP64 (sums in FP64 of the stored values).
+// e - e_ref and q of one node in the compute type (Eqs. 53-54).
 template <typename C>
-__device__ __forceinline__ void node_moments_f64(const C (&d)[8], const Readout &r, double &de,
-                                                 double &qx, double &qy) {
-    double v[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = (double)d[i];
-    const double rho = ((v[0] + v[2]) + (v[1] + v[3])) + ((v[4] + v[6]) + (v[5] + v[7]));
-    const double mx = (v[0] - v[2]) + (v[4] - v[6]) + (v[7] - v[5]);
-    const double my = (v[1] - v[3]) + (v[4] - v[6]) + (v[5] - v[7]);
-    de = rho * r.inv_scale;
-    qx = r.kappa * mx * r.inv_scale;
-    qy = r.kappa * my * r.inv_scale;
+__device__ __forceinline__ void node_moments(const C (&d)[8], const Coef<C> &k, C inv_s, C &de,
+                                             C &qx, C &qy) {
+    const C rho = ((d[0] + d[2]) + (d[1] + d[3])) + ((d[4] + d[6]) + (d[5] + d[7]));
+    const C mx = (d[0] - d[2]) + (d[4] - d[6]) + (d[7] - d[5]);
+    const C my = (d[1] - d[3]) + (d[4] - d[6]) + (d[5] - d[7]);
+    de = rho * inv_s;
+    qx = (mx - k.lambda * mx) * inv_s;
+    qy = (my - k.lambda * my) * inv_s;
 }
 
+// ---------------------------------------------------------------------------
+// Scalar read-outs (any nx).  Loops are warp-uniform so warp shuffles are
+// legal inside them.
 template <typename T>
-__global__ void moments_kernel(const T *__restrict__ src, Readout r,
-                               Coef<typename Store<T>::C> k, double *e, double *qx,
-                               double *qy) {
+__global__ void moments_scalar(const T *__restrict__ src, Readout r,
+                               Coef<typename Store<T>::C> k, double *e, double *qx, double *qy) {
     using C = typename Store<T>::C;
     const long long n = (long long)r.nx * r.ny;
+    const C inv_s = (C)r.inv_scale;
     for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < n;
          node += (long long)gridDim.x * blockDim.x) {
         const int y = int(node / r.nx), x = int(node - (long long)y * r.nx);
         C d[8];
         state_node<T>(src, r, k, x, y, d);
-        double de, a, b;
-        node_moments_f64(d, r, de, a, b);
-        if (e) e[node] = r.e_ref + de;
-        if (qx) qx[node] = a;
-        if (qy) qy[node] = b;
+        C de, a, b;
+        node_moments(d, k, inv_s, de, a, b);
+        if (e) e[node] = r.e_ref + (double)de;
+        if (qx) qx[node] = (double)a;
+        if (qy) qy[node] = (double)b;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+residual_scalar(const T *__restrict__ src, Readout r, Coef<typename Store<T>::C> k,
+                typename Store<T>::C *__restrict__ prev, int have_prev,
+                double *__restrict__ partials) {
+    using C = typename Store<T>::C;
+    const long long n = (long long)r.nx * r.ny;
+    const C inv_s = (C)r.inv_scale;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const long long node = base + (threadIdx.x & 31);
+        C loc[5] = {C(0), C(0), C(0), C(0), C(0)};
+        if (node < n) {
+            const int y = int(node / r.nx), x = int(node - (long long)y * r.nx);
+            C d[8];
+            state_node<T>(src, r, k, x, y, d);
+            residual_node(d, k, inv_s, prev, n, node, have_prev != 0, loc);
+        }
+        warp_flush_residual(loc, acc);
+    }
+    block_sum5_lane0(acc, partials + (size_t)blockIdx.x * 5);
+}
+
+// ---------------------------------------------------------------------------
+// Vectorised read-outs (nx % V == 0): one thread per 16-byte vector of nodes,
+// the same pull (and so the same node-to-warp grouping of the residual sums)
+// as the vector stream-collide kernel.
+enum { READ_MOMENTS = 0, READ_RESIDUAL = 1 };
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+readout_vector(const T *__restrict__ src, Readout r, Coef<typename Store<T>::C> k, double *e,
+               double *qx, double *qy, typename Store<T>::C *__restrict__ prev, int have_prev,
+               double *__restrict__ partials) {
+    using C = typename Store<T>::C;
+    constexpr int V = Pack<T>::V;
+    const long long plane = (long long)r.nx * r.ny;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const C inv_s = (C)r.inv_scale;
+    C d[8][V];
+    const VecPos p = r.pulled ? vector_pull<T>(src, r.nx, r.ny, plane, r.bc_x, r.bc_y, k, t, d)
+                              : vector_local<T>(src, r.nx, r.ny, plane, t, d);
+    C loc[5] = {C(0), C(0), C(0), C(0), C(0)};
+    if (p.active) {
+        const long long out = (long long)p.y * r.nx + p.x0;
+        C n[V][8];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) n[j][i] = d[i][j];
+            if (p.bottom) wall_bottom(n[j], k);
+            if (p.top) wall_top(n[j], k);
+            if (MODE == READ_MOMENTS) {
+                C de, a, b;
+                node_moments(n[j], k, inv_s, de, a, b);
+                if (e) e[out + j] = r.e_ref + (double)de;
+                if (qx) qx[out + j] = (double)a;
+                if (qy) qy[out + j] = (double)b;
+            }
+        }
+        if (MODE == READ_RESIDUAL)
+            residual_vec<C, V>(n, k, inv_s, prev, plane, out, have_prev != 0, loc);
+    }
+    if (MODE == READ_RESIDUAL) {
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        warp_flush_residual(loc, acc);
+        block_sum5_lane0(acc, partials + (size_t)blockIdx.x * 5);
     }
 }
 
@@ -74,24 +149,6 @@ __global__ void populations_kernel(const T *__restrict__ src, Readout r,
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256)
-residual_kernel(const T *__restrict__ src, Readout r, Coef<typename Store<T>::C> k,
-                typename Store<T>::C *__restrict__ prev, int have_prev,
-                double *__restrict__ partials) {
-    using C = typename Store<T>::C;
-    const long long n = (long long)r.nx * r.ny;
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < n;
-         node += (long long)gridDim.x * blockDim.x) {
-        const int y = int(node / r.nx), x = int(node - (long long)y * r.nx);
-        C d[8];
-        state_node<T>(src, r, k, x, y, d);
-        residual_node(d, k, (C)r.inv_scale, prev, n, node, have_prev != 0, acc);
-    }
-    block_sum5_store(acc, partials + (size_t)blockIdx.x * 5);
-}
-
 // Fixed-order sum of the per-block partials (deterministic result).
 __global__ void __launch_bounds__(256) finalize_sums(const double *__restrict__ partials,
                                                      int blocks, double *__restrict__ sums) {
@@ -103,6 +160,9 @@ __global__ void __launch_bounds__(256) finalize_sums(const double *__restrict__ 
     block_sum5_store(acc, sums);
 }
 
+// Eq. 15 on deviations, in the compute type: d_i = s (w_i (e - e_ref) +
+// (5/3) a_i c_i.q), written as the state of step 0 into `pre` and, collided,
+// into `post`.
 template <typename T>
 __global__ void init_kernel(const double *__restrict__ e, const double *__restrict__ qx,
                             const double *__restrict__ qy, int nx, int ny, double e_ref,
@@ -110,24 +170,22 @@ __global__ void init_kernel(const double *__restrict__ e, const double *__restri
                             T *__restrict__ post) {
     using C = typename Store<T>::C;
     const long long n = (long long)nx * ny;
+    const C s = (C)scale;
     for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < n;
          node += (long long)gridDim.x * blockDim.x) {
-        const double de = e[node] - e_ref;
-        const double a = qx ? qx[node] : 0.0;
-        const double b = qy ? qy[node] : 0.0;
-        // Eq. 15 on deviations: w_i (e - e_ref) + (5/3) a_i c_i.q, times s;
-        // (5/3) a_i = 1/3 (axis) or 1/12 (diagonal).
-        const double dv[8] = {
-            (2.0 / 9.0) * de + a / 3.0,          (2.0 / 9.0) * de + b / 3.0,
-            (2.0 / 9.0) * de - a / 3.0,          (2.0 / 9.0) * de - b / 3.0,
-            (1.0 / 36.0) * de + (a + b) / 12.0,  (1.0 / 36.0) * de + (b - a) / 12.0,
-            (1.0 / 36.0) * de - (a + b) / 12.0,  (1.0 / 36.0) * de + (a - b) / 12.0};
+        const C de = (C)(e[node] - e_ref);
+        const C a = qx ? (C)qx[node] : C(0);
+        const C b = qy ? (C)qy[node] : C(0);
+        const C wa = k.w_axis * de, wd = k.w_diag * de;
+        const C ta = k.h_axis * a, tb = k.h_axis * b;
+        const C tp = k.h_diag * (a + b), tm = k.h_diag * (a - b);
+        const C dv[8] = {wa + ta, wa + tb, wa - ta, wa - tb, wd + tp, wd - tm, wd - tp, wd + tm};
         C d[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const T s = Store<T>::put((C)(dv[i] * scale));
-            pre[(long long)i * n + node] = s;
-            d[i] = Store<T>::load(s);
+            const T v = Store<T>::put(dv[i] * s);
+            pre[(long long)i * n + node] = v;
+            d[i] = Store<T>::load(v);
         }
         collide(d, k);
 #pragma unroll
@@ -135,21 +193,24 @@ __global__ void init_kernel(const double *__restrict__ e, const double *__restri
     }
 }
 
+// Largest per-node bound (2/9)|e - e_ref| + (1/3)(|qx| + |qy|) >= max |d_i|
+// (unscaled), in FP32, maxed per warp; non-finite input -> +inf.
 __global__ void max_deviation_kernel(const double *__restrict__ e, const double *__restrict__ qx,
                                      const double *__restrict__ qy, long long n, double e_ref,
                                      unsigned long long *out) {
-    double m = 0.0;
+    float m = 0.f;
     for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < n;
          node += (long long)gridDim.x * blockDim.x) {
-        double v = (2.0 / 9.0) * fabs(e[node] - e_ref);
-        if (qx) v += fabs(qx[node]) / 3.0;
-        if (qy) v += fabs(qy[node]) / 3.0;
-        m = isfinite(v) ? fmax(m, v) : HUGE_VAL;   // non-finite input -> +inf
+        float v = (2.0f / 9.0f) * fabsf((float)(e[node] - e_ref));
+        if (qx) v += fabsf((float)qx[node]) / 3.0f;
+        if (qy) v += fabsf((float)qy[node]) / 3.0f;
+        m = isfinite(v) ? fmaxf(m, v) : INFINITY;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     // non-negative doubles order like their bit patterns
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, (unsigned long long)__double_as_longlong((double)m));
 }
 
 static unsigned grid_for(long long n, int threads) {
@@ -158,11 +219,29 @@ static unsigned grid_for(long long n, int threads) {
     return (unsigned)(b > 0 ? b : 1);
 }
 
+template <typename T> static bool vec_ok(const Readout &r) { return r.nx % Pack<T>::V == 0; }
+
+template <typename T> static unsigned vec_blocks(const Readout &r) {
+    const long long threads = (long long)r.nx * r.ny / Pack<T>::V;
+    return (unsigned)((threads + 255) / 256);
+}
+
+long long readout_blocks(int precision, int nx, int ny) {
+    const long long plane = (long long)nx * ny;
+    const int v = vector_width(precision);
+    if (nx % v) return RESIDUAL_BLOCKS;
+    return (plane / v + 255) / 256;
+}
+
 template <typename T>
 cudaError_t launch_moments(const T *src, const Readout &r, const Coef<typename Store<T>::C> &k,
                            double *e, double *qx, double *qy, cudaStream_t stream) {
-    moments_kernel<T><<<grid_for((long long)r.nx * r.ny, 256), 256, 0, stream>>>(src, r, k, e,
-                                                                               qx, qy);
+    if (vec_ok<T>(r))
+        readout_vector<T, READ_MOMENTS><<<vec_blocks<T>(r), 256, 0, stream>>>(
+            src, r, k, e, qx, qy, nullptr, 0, nullptr);
+    else
+        moments_scalar<T><<<grid_for((long long)r.nx * r.ny, 256), 256, 0, stream>>>(src, r, k,
+                                                                                   e, qx, qy);
     return cudaGetLastError();
 }
 
@@ -179,11 +258,19 @@ template <typename T>
 cudaError_t launch_residual(const T *src, const Readout &r, const Coef<typename Store<T>::C> &k,
                             typename Store<T>::C *prev, bool have_prev, double *partials,
                             double *sums, cudaStream_t stream) {
-    residual_kernel<T><<<RESIDUAL_BLOCKS, 256, 0, stream>>>(src, r, k, prev, have_prev ? 1 : 0,
-                                                            partials);
+    int blocks;
+    if (vec_ok<T>(r)) {
+        blocks = (int)vec_blocks<T>(r);
+        readout_vector<T, READ_RESIDUAL><<<blocks, 256, 0, stream>>>(
+            src, r, k, nullptr, nullptr, nullptr, prev, have_prev ? 1 : 0, partials);
+    } else {
+        blocks = RESIDUAL_BLOCKS;
+        residual_scalar<T><<<blocks, 256, 0, stream>>>(src, r, k, prev, have_prev ? 1 : 0,
+                                                       partials);
+    }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    return launch_finalize(partials, RESIDUAL_BLOCKS, sums, stream);
+    return launch_finalize(partials, blocks, sums, stream);
 }
 
 cudaError_t launch_finalize(const double *partials, int blocks, double *sums,

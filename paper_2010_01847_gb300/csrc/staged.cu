@@ -182,11 +182,11 @@ template <typename T, int CW> constexpr int stage_bytes() {
 
 // 16-bit storage keeps 8 nodes per consumer thread; asking for two CTAs per
 // SM caps its registers so two rings fit on an SM.
-template <typename T, int CW, bool RES>
+template <typename T, int CW>
 __global__ void __launch_bounds__((CW + 1) * 32, (sizeof(T) == 2 ? 2 : 1))
 step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long long plane,
             int bc_x, int bc_y, int stages, int hinted, Coef<typename Store<T>::C> k,
-            int *status, ResidualReq<typename Store<T>::C> rq) {
+            int *status) {
     using C = typename Store<T>::C;
     constexpr int V = Vec16<T>::V;
     constexpr int W = tile_width<T, CW>();
@@ -210,8 +210,6 @@ step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 
     if (warp == CW) {
         // ---------------- producer ----------------
@@ -295,8 +293,6 @@ step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long
                 for (int i = 0; i < 8; ++i) n[i] = d[i][j];
                 if (bottom) wall_bottom(n, k);
                 if (top) wall_top(n, k);
-                if (RES) residual_node(n, k, rq.inv_scale, rq.prev, plane, out + j,
-                                       rq.have_prev != 0, acc);
                 collide(n, k);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) d[i][j] = n[i];
@@ -305,10 +301,6 @@ step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long
             for (int i = 0; i < 8; ++i)
                 st_stream(dst + (long long)i * plane + out, Vec16<T>::pack(d[i]));
         }
-    }
-    if (RES) {
-        __syncthreads();
-        block_sum5_store(acc, rq.partials + (size_t)blockIdx.x * 5);
     }
 }
 
@@ -324,9 +316,7 @@ template <typename T> constexpr int prec_of() {
            : (std::is_same<T, __half>::value ? PREC_FP16 : PREC_BF16);
 }
 
-template <typename T, int CW, bool RES> constexpr auto kernel_of() {
-    return step_staged<T, CW, RES>;
-}
+template <typename T, int CW> constexpr auto kernel_of() { return step_staged<T, CW>; }
 
 struct DeviceInfo {
     int sms = 0;
@@ -349,11 +339,8 @@ cudaError_t prepare(int dev) {
         if (e != cudaSuccess) return e;
         const int want = (int)smem_bytes<T, CW>(MAX_STAGES) + 2048;
         const int limit = want < optin ? want : optin;
-        e = cudaFuncSetAttribute(kernel_of<T, CW, false>(),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(kernel_of<T, CW, true>(),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+        e = cudaFuncSetAttribute(kernel_of<T, CW>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 limit);
         if (e != cudaSuccess) return e;
         info.prepared[prec_of<T>()][vi] = true;
     }
@@ -369,7 +356,7 @@ cudaError_t plan_for(int stages, int ctas_per_sm, int hint, StagedPlan *out) {
     if (stages < 2 || stages > MAX_STAGES) return cudaErrorInvalidValue;
     if ((e = prepare<T, CW>(dev)) != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_of<T, CW, false>(),
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_of<T, CW>(),
                                                       (CW + 1) * 32, smem_bytes<T, CW>(stages));
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -384,22 +371,16 @@ cudaError_t plan_for(int stages, int ctas_per_sm, int hint, StagedPlan *out) {
 
 template <typename T, int CW>
 cudaError_t launch_cw(const T *src, T *dst, int nx, int ny, int bc_x, int bc_y,
-                      const Coef<typename Store<T>::C> &k, int *status,
-                      const ResidualReq<typename Store<T>::C> *rq, const StagedPlan &plan,
+                      const Coef<typename Store<T>::C> &k, int *status, const StagedPlan &plan,
                       int *blocks_out, cudaStream_t stream) {
     const long long plane = (long long)nx * ny;
     const long long n_tiles = (long long)(nx / tile_width<T, CW>()) * ny;
     const int grid = (int)(n_tiles < plan.grid ? n_tiles : plan.grid);
     const size_t smem = smem_bytes<T, CW>(plan.stages);
     if (blocks_out) *blocks_out = grid;
-    if (rq) {
-        step_staged<T, CW, true><<<grid, (CW + 1) * 32, smem, stream>>>(
-            src, dst, nx, ny, plane, bc_x, bc_y, plan.stages, plan.hint, k, status, *rq);
-    } else {
-        ResidualReq<typename Store<T>::C> none{};
-        step_staged<T, CW, false><<<grid, (CW + 1) * 32, smem, stream>>>(
-            src, dst, nx, ny, plane, bc_x, bc_y, plan.stages, plan.hint, k, status, none);
-    }
+    step_staged<T, CW><<<grid, (CW + 1) * 32, smem, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                             bc_y, plan.stages, plan.hint, k,
+                                                             status);
     return cudaGetLastError();
 }
 
@@ -439,18 +420,15 @@ cudaError_t staged_plan(int precision, int stages, int ctas_per_sm, int consumer
 template <typename T>
 cudaError_t launch_step_staged(const T *src, T *dst, int nx, int ny, int bc_x, int bc_y,
                                const Coef<typename Store<T>::C> &k, int *status,
-                               const ResidualReq<typename Store<T>::C> *rq,
                                const StagedPlan &plan, int *blocks_out, cudaStream_t stream) {
     if (plan.consumer_warps == 4)
-        return launch_cw<T, 4>(src, dst, nx, ny, bc_x, bc_y, k, status, rq, plan, blocks_out,
-                               stream);
-    return launch_cw<T, 8>(src, dst, nx, ny, bc_x, bc_y, k, status, rq, plan, blocks_out, stream);
+        return launch_cw<T, 4>(src, dst, nx, ny, bc_x, bc_y, k, status, plan, blocks_out, stream);
+    return launch_cw<T, 8>(src, dst, nx, ny, bc_x, bc_y, k, status, plan, blocks_out, stream);
 }
 
 #define PLBM_STAGED(T)                                                                       \
     template cudaError_t launch_step_staged<T>(const T *, T *, int, int, int, int,           \
                                                const Coef<Store<T>::C> &, int *,             \
-                                               const ResidualReq<Store<T>::C> *,             \
                                                const StagedPlan &, int *, cudaStream_t);
 PLBM_STAGED(float)
 PLBM_STAGED(double)
