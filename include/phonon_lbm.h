@@ -248,6 +248,81 @@ double lbm_storage_scale(const lbm_ctx *ctx);
  * lbm_create when ctx is NULL).  Never NULL; valid until the next call. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
+/* ---- Batched solver ------------------------------------------------------
+ * Many independent lattices ("instances", e.g. channels of different width
+ * and Knudsen numbers) advanced together: every lbm_batch step is ONE
+ * persistent kernel launch over a list of work items (instance, run of
+ * 16-byte vectors) of all running instances, with each instance's own
+ * coefficients (same scheme and boundaries as a single context).  The
+ * steady-state solve replays a captured CUDA graph per check window and
+ * retires converged instances on the device's work list. */
+typedef struct {
+    int nx, ny;              /* nx a positive multiple of 16 / element size    */
+    double tau_N, tau_R;     /* lattice steps, as lbm_create                   */
+    lbm_boundary bc;         /* as lbm_create                                  */
+} lbm_instance;
+
+typedef struct lbm_batch lbm_batch;
+
+/* Create a batch of `count` instances sharing a storage kind, reference
+ * energy and stream.  Allocates two packed population buffers, the residual
+ * history and the work list.  Errors: EINVAL / EUNSUPPORTED per instance
+ * (text names the instance), ENOMEM, ECUDA. */
+lbm_status lbm_batch_create(const lbm_instance *inst, int count, lbm_precision precision,
+                            double e_ref, void *stream, lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *batch);
+
+/* Step 0 of every instance (Eq. 15) from HOST fields concatenated in
+ * instance order (instance i: ny_i*nx_i values, row-major).  e NULL = e_ref
+ * everywhere (the cold start); qx/qy NULL = 0.  Resets step counts, residual
+ * history and retirement (every instance runs again).  Synchronous. */
+lbm_status lbm_batch_init(lbm_batch *batch, const double *e, const double *qx,
+                          const double *qy);
+
+/* Advance every running instance n steps (n launches).  Async. */
+lbm_status lbm_batch_step(lbm_batch *batch, long n);
+
+/* Residual (definitions of lbm_residual, history per instance) and total
+ * energy of every running instance; arrays of `count` (either may be NULL;
+ * retired instances keep their last residual, energy left untouched).
+ * Needs at least one step since lbm_batch_init (EUNSUPPORTED otherwise).
+ * Synchronous.  ENONFINITE when an instance holds NaN/Inf. */
+lbm_status lbm_batch_residuals(lbm_batch *batch, double *r, double *energy);
+
+/* Run to steady state: windows of check_every (even, >= 2) steps, the last
+ * step of each reducing every running instance's residual inside its
+ * launch; an instance retires once r < tol on two consecutive checks, or
+ * when it reaches max_steps.  Outputs (arrays of `count`, may be NULL): the
+ * steps each instance ran and its last residual.  Synchronous.  ENONFINITE
+ * when an instance became non-finite (it is retired, r = NaN). */
+lbm_status lbm_batch_solve(lbm_batch *batch, double tol, int check_every, long max_steps,
+                           long *steps, double *r);
+
+/* e and q of instance i's current state into HOST arrays [ny_i][nx_i]
+ * (any may be NULL).  Synchronous. */
+lbm_status lbm_batch_moments(lbm_batch *batch, int i, double *e, double *qx, double *qy);
+
+/* Work schedule: threads per work item (128, 256 or 512: tile of
+ * threads x 16-byte vectors of one instance) and persistent CTAs per SM
+ * (0 = as many as fit).  Results do not depend on it. */
+lbm_status lbm_batch_set_schedule(lbm_batch *batch, int threads_per_item, int ctas_per_sm);
+lbm_status lbm_batch_get_schedule(const lbm_batch *batch, int *threads_per_item,
+                                  int *ctas_per_sm, int *grid);
+
+/* Autotuner: times every schedule above (trial_steps steps each, 0 = 10)
+ * on the initialised batch, keeps the fastest; the state is copied aside
+ * (2 x population bytes of temporary device memory) and restored.
+ * Synchronous. */
+lbm_status lbm_batch_autotune(lbm_batch *batch, int trial_steps, double *us_per_step);
+
+/* Running (not retired) instances, and the steps instance i has run. */
+long lbm_batch_active(const lbm_batch *batch);
+long lbm_batch_steps(const lbm_batch *batch, int i);
+
+/* Text of the batch's last failure (of the last failed lbm_batch_create via
+ * lbm_last_error(NULL)). */
+const char *lbm_batch_last_error(const lbm_batch *batch);
+
 /* ---- Residual without device allocation ---------------------------------
  * The paper has no counterpart to this call; it serves callers that must not
  * allocate device memory while they run: a host application that reserved

@@ -40,6 +40,10 @@ EXPORTS = [
     "lbm_set_kernel", "lbm_get_kernel", "lbm_set_staged_config", "lbm_get_staged_config",
     "lbm_set_graph_chunk", "lbm_autotune",
     "lbm_kernel_launches", "lbm_storage_scale", "lbm_last_error",
+    "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_init", "lbm_batch_step",
+    "lbm_batch_residuals", "lbm_batch_solve", "lbm_batch_moments", "lbm_batch_set_schedule",
+    "lbm_batch_get_schedule", "lbm_batch_autotune", "lbm_batch_active", "lbm_batch_steps",
+    "lbm_batch_last_error",
     "lbm_residual_noalloc",
 ]
 NOALLOC_MAX_NODES = 16777216
@@ -57,6 +61,11 @@ class Grid(ctypes.Structure):
 
 class Boundary(ctypes.Structure):
     _fields_ = [("x", ctypes.c_int), ("y", ctypes.c_int), ("delta_e", ctypes.c_double)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("tau_N", ctypes.c_double),
+                ("tau_R", ctypes.c_double), ("bc", Boundary)]
 
 
 _lib = None
@@ -106,6 +115,21 @@ def load_library(path: str = LIB_PATH):
         "lbm_kernel_launches": (ctypes.c_longlong, [vp]),
         "lbm_storage_scale": (ctypes.c_double, [vp]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_batch_create": (st, [ctypes.POINTER(Instance), ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_double, vp, ctypes.POINTER(vp)]),
+        "lbm_batch_destroy": (None, [vp]),
+        "lbm_batch_init": (st, [vp, dp, dp, dp]),
+        "lbm_batch_step": (st, [vp, c_long]),
+        "lbm_batch_residuals": (st, [vp, dp, dp]),
+        "lbm_batch_solve": (st, [vp, ctypes.c_double, ctypes.c_int, c_long,
+                                 ctypes.POINTER(c_long), dp]),
+        "lbm_batch_moments": (st, [vp, ctypes.c_int, dp, dp, dp]),
+        "lbm_batch_set_schedule": (st, [vp, ctypes.c_int, ctypes.c_int]),
+        "lbm_batch_get_schedule": (st, [vp] + [ctypes.POINTER(ctypes.c_int)] * 3),
+        "lbm_batch_autotune": (st, [vp, ctypes.c_int, dp]),
+        "lbm_batch_active": (c_long, [vp]),
+        "lbm_batch_steps": (c_long, [vp, ctypes.c_int]),
+        "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
         "lbm_residual_noalloc": (st, [vp, vp, vp, vp, vp, vp, ctypes.c_longlong,
                                       ctypes.c_double, c_long, vp, dp, dp]),
     }
@@ -353,3 +377,109 @@ class Lattice:
     def bytes_per_site_update(self) -> int:
         """Algorithmic bytes per site update: 8 populations read + 8 written."""
         return 16 * _ELEM[self.precision]
+
+
+class Batch:
+    """Many independent lattices advanced by one launch per step (see the
+    batched solver in include/phonon_lbm.h).  ``instances`` is a list of
+    dicts with keys nx, ny, tau_N, tau_R and optional bc_x, bc_y, delta_e."""
+
+    def __init__(self, instances, precision="fp32", e_ref=1.0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the phonon LBM runs only on the GPU")
+        self._lib = load_library()
+        self.torch = torch
+        self.instances = [dict(i) for i in instances]
+        arr = (Instance * len(instances))()
+        for a, i in zip(arr, self.instances):
+            a.nx, a.ny = int(i["nx"]), int(i["ny"])
+            a.tau_N, a.tau_R = float(i["tau_N"]), float(i["tau_R"])
+            a.bc = Boundary(int(i.get("bc_x", PERIODIC)), int(i.get("bc_y", PERIODIC)),
+                            float(i.get("delta_e", 0.0)))
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.stream = torch.cuda.current_stream()
+        self._b = ctypes.c_void_p()
+        st = self._lib.lbm_batch_create(arr, len(instances), self.precision, float(e_ref),
+                                        ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(self._b))
+        if st != OK:
+            self._b = ctypes.c_void_p()
+            raise LBMError(st, self._lib.lbm_last_error(None).decode())
+
+    def _check(self, st):
+        if st != OK:
+            raise LBMError(st, self._lib.lbm_batch_last_error(self._b).decode())
+
+    def close(self):
+        if self._b:
+            self._lib.lbm_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def count(self):
+        return len(self.instances)
+
+    def init(self, e=None, qx=None, qy=None):
+        """Step 0 from per-instance host fields (lists of [ny, nx] arrays) or
+        the cold start (e = e_ref, q = 0) when omitted."""
+        def cat(fields):
+            if fields is None:
+                return None
+            return np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.float64).ravel()
+                                                        for f in fields]))
+        e, qx, qy = cat(e), cat(qx), cat(qy)
+        p = lambda a: _dptr(a) if a is not None else None
+        self._check(self._lib.lbm_batch_init(self._b, p(e), p(qx), p(qy)))
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_batch_step(self._b, int(n)))
+
+    def residuals(self):
+        r = np.empty(self.count)
+        en = np.full(self.count, np.nan)
+        self._check(self._lib.lbm_batch_residuals(self._b, _dptr(r), _dptr(en)))
+        return r, en
+
+    def solve(self, tol=1e-8, check_every=100, max_steps=10 ** 6):
+        steps = (ctypes.c_long * self.count)()
+        r = np.empty(self.count)
+        self._check(self._lib.lbm_batch_solve(self._b, float(tol), int(check_every),
+                                              int(max_steps), steps, _dptr(r)))
+        return np.array(steps[:], dtype=np.int64), r
+
+    def moments(self, i):
+        nx, ny = self.instances[i]["nx"], self.instances[i]["ny"]
+        e = np.empty((ny, nx))
+        qx = np.empty_like(e)
+        qy = np.empty_like(e)
+        self._check(self._lib.lbm_batch_moments(self._b, int(i), _dptr(e), _dptr(qx), _dptr(qy)))
+        return e, qx, qy
+
+    def set_schedule(self, threads_per_item=256, ctas_per_sm=0):
+        self._check(self._lib.lbm_batch_set_schedule(self._b, int(threads_per_item),
+                                                     int(ctas_per_sm)))
+
+    @property
+    def schedule(self):
+        v = [ctypes.c_int() for _ in range(3)]
+        self._check(self._lib.lbm_batch_get_schedule(self._b, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("threads_per_item", "ctas_per_sm", "grid"), (x.value for x in v)))
+
+    def autotune(self, trial_steps=10):
+        us = ctypes.c_double()
+        self._check(self._lib.lbm_batch_autotune(self._b, int(trial_steps), ctypes.byref(us)))
+        return us.value
+
+    @property
+    def active(self):
+        return self._lib.lbm_batch_active(self._b)
+
+    def steps_of(self, i):
+        return self._lib.lbm_batch_steps(self._b, int(i))

@@ -1,0 +1,905 @@
+// Batched solver: many independent lattices ("instances") of uneven size and
+// relaxation times advanced together, one launch per time step for all of
+// them, run to steady state with per-instance residuals and retirement.
+//
+// Layout: the instances' population planes are packed one after another in
+// two shared buffers (instance i: 8 planes of nx_i * ny_i elements starting
+// at element off_i); residual histories likewise (3 planes of the compute
+// type per instance).  Work is cut into items of `tpi` threads x V nodes of
+// one instance; a persistent grid walks the list of items of the instances
+// still running.  Each item runs the same vectorised pull, boundary and
+// collision as the single-lattice vector kernel (Eqs. 13, 15, 16, 53-54, 58,
+// 59-60) with its instance's coefficients.
+//
+// Steady-state solve: windows of K (even) steps are captured once as a CUDA
+// graph -- K-1 plain step launches, one step launch that also reduces each
+// item's residual sums, a per-instance fixed-order sum, and the copy of the
+// sums to pinned host memory.  Between windows the host retires instances
+// whose residual stayed below the tolerance on two consecutive checks and
+// uploads the shorter item list; the graph reads the list and its length
+// from device memory, so it is replayed unchanged.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/phonon_lbm.h"
+#include "lbm_kernels.h"
+#include "vector_pull.cuh"
+
+namespace plbm {
+namespace {
+
+enum { B_STEP = 0, B_STEP_RES = 1, B_RES_ONLY = 2 };
+
+template <typename C>
+struct InstDev {
+    long long off;       // element offset of plane 0 in the population buffers
+    long long hoff;      // element offset of the history planes
+    long long plane;     // nx * ny
+    int nx, ny, bc_x, bc_y;
+    Coef<C> k;
+};
+
+struct Item {
+    int inst;            // instance index
+    int first;           // first thread (vector) index within the instance
+};
+
+struct Range {
+    int inst, begin, end;   // items [begin, end) of an active instance
+};
+
+// Block-wide sum of per-warp values (lane 0 of each warp); reusable inside a
+// block-uniform loop.
+__device__ __forceinline__ void item_sum5(const double (&v)[5], double *out) {
+    __shared__ double sh[5][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) sh[q][warp] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[q][w];
+            out[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512)
+batch_kernel(const T *__restrict__ src, T *__restrict__ dst,
+             const InstDev<typename Store<T>::C> *__restrict__ inst,
+             const Item *__restrict__ items, const int *__restrict__ n_items,
+             typename Store<T>::C inv_s, typename Store<T>::C *__restrict__ hist, int have_prev,
+             double *__restrict__ partials) {
+    using C = typename Store<T>::C;
+    constexpr int V = Pack<T>::V;
+    const int count = *n_items;
+    for (int it = blockIdx.x; it < count; it += gridDim.x) {
+        const Item item = items[it];
+        const InstDev<C> I = inst[item.inst];
+        const long long t = (long long)item.first + threadIdx.x;
+        C d[8][V];
+        const VecPos p = vector_pull<T>(src + I.off, I.nx, I.ny, I.plane, I.bc_x, I.bc_y, I.k, t,
+                                        d);
+        C loc[5] = {C(0), C(0), C(0), C(0), C(0)};
+        if (p.active) {
+            const long long out = (long long)p.y * I.nx + p.x0;
+            C n[V][8];
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) n[j][i] = d[i][j];
+                if (p.bottom) wall_bottom(n[j], I.k);
+                if (p.top) wall_top(n[j], I.k);
+            }
+            if (MODE != B_STEP)
+                residual_vec<C, V>(n, I.k, inv_s, hist + I.hoff, I.plane, out, have_prev != 0,
+                                   loc);
+            if (MODE != B_RES_ONLY) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    collide(n[j], I.k);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) d[i][j] = n[j][i];
+                }
+                T *o = dst + I.off;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    st_stream(o + (long long)i * I.plane + out, Pack<T>::pack(d[i]));
+            }
+        }
+        if (MODE != B_STEP) {
+            double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            warp_flush_residual(loc, acc);
+            item_sum5(acc, partials + (size_t)it * 5);
+        }
+    }
+}
+
+// One block per active instance: fixed-order sum of its items' partials.
+__global__ void __launch_bounds__(128)
+batch_finalize(const double *__restrict__ partials, const Range *__restrict__ ranges,
+               const int *__restrict__ n_ranges, double *__restrict__ sums) {
+    if ((int)blockIdx.x >= *n_ranges) return;
+    const Range r = ranges[blockIdx.x];
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = r.begin + threadIdx.x; b < r.end; b += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[q] += partials[(size_t)b * 5 + q];
+    }
+    block_sum5_store(acc, sums + (size_t)r.inst * 5);
+}
+
+}  // namespace
+}  // namespace plbm
+
+using namespace plbm;
+
+struct lbm_batch {
+    int device = 0;
+    int count = 0;
+    int precision = 0;
+    double e_ref = 1.0;
+    double scale = 1.0;
+    cudaStream_t stream = nullptr;
+    std::vector<lbm_instance> inst;
+    std::vector<long long> off, hoff;
+    long long total = 0, htotal = 0, max_plane = 0;
+    void *buf[2] = {nullptr, nullptr};
+    void *hist = nullptr;
+    void *dinst = nullptr;           // InstDev<C>[count]
+    Item *ditems = nullptr;
+    Range *dranges = nullptr;
+    int *dcounts = nullptr;          // [0] items, [1] ranges
+    double *partials = nullptr;      // 5 per item
+    double *dsums = nullptr;         // 5 per instance
+    double *hsums = nullptr;         // pinned host copy
+    Item *hitems = nullptr;          // pinned host staging
+    Range *hranges = nullptr;
+    int *hcounts = nullptr;
+    long long max_items = 0;
+    int n_items = 0, n_ranges = 0;
+    double *fields = nullptr;        // init staging, 3 x max_plane doubles
+    unsigned long long *maxbits = nullptr;
+    int cur = 0;
+    bool initialised = false;
+    std::vector<char> active;
+    std::vector<int> icur;           // buffer parity of each instance's last step
+    std::vector<long> steps;
+    std::vector<long> prev_step;
+    std::vector<int> good;
+    std::vector<double> last_r;
+    bool have_prev = false;
+    int tpi = 256;                   // threads per work item
+    int ctas_per_sm = 0;             // 0 = as many as fit
+    int grid = 0;
+    int sms = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_k = 0;
+    int graph_parity = 0;
+    std::string err;
+};
+
+namespace {
+
+size_t elem_size(int p) { return p == PREC_FP32 ? 4 : p == PREC_FP64 ? 8 : 2; }
+size_t csize(int p) { return p == PREC_FP64 ? 8 : 4; }
+
+lbm_status bfail(lbm_batch *b, lbm_status s, const std::string &m) {
+    if (b) b->err = m;
+    else set_global_error(m.c_str());
+    return s;
+}
+
+lbm_status bcuda(lbm_batch *b, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                    cudaGetErrorString(e) + ")";
+    (void)cudaGetLastError();
+    return bfail(b, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, m);
+}
+
+#define BCK(b, call)                                              \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return bcuda(b, e_, #call);        \
+    } while (0)
+
+struct BGuard {
+    int old = -1;
+    explicit BGuard(int dev) {
+        if (cudaGetDevice(&old) == cudaSuccess && old != dev) cudaSetDevice(dev);
+        else old = -1;
+    }
+    ~BGuard() {
+        if (old >= 0) cudaSetDevice(old);
+    }
+};
+
+struct Params {
+    double tau, tau_r, sigma, lambda, kappa;
+};
+
+Params params_of(const lbm_instance &in) {
+    Params p;
+    const double inv_c = (std::isinf(in.tau_N) ? 0.0 : 1.0 / in.tau_N) +
+                         (std::isinf(in.tau_R) ? 0.0 : 1.0 / in.tau_R);
+    p.tau = 1.0 / inv_c + 0.5;                                        // Eq. 49
+    p.tau_r = in.tau_R;
+    p.sigma = std::isinf(in.tau_R) ? 0.0 : (1.0 - 1.0 / (2.0 * p.tau)) / in.tau_R;   // Eq. 16
+    p.lambda = std::isinf(in.tau_R) ? 0.0 : 1.0 / (2.0 * in.tau_R + 1.0);         // Eq. 54
+    p.kappa = 1.0 - p.lambda;
+    return p;
+}
+
+template <typename C>
+Coef<C> coef_of(const lbm_instance &in, double scale) {
+    const Params p = params_of(in);
+    Coef<C> k;
+    k.omega = (C)(1.0 / p.tau);
+    k.sigma = (C)p.sigma;
+    k.lambda = (C)p.lambda;
+    k.w_axis = (C)(2.0 / 9.0);
+    k.w_diag = (C)0.25 - k.w_axis;
+    k.h_axis = (C)(1.0 / 3.0);
+    k.h_diag = ((C)1 - (C)2 * k.h_axis) / (C)4;
+    k.u_axis = (C)0.8;
+    k.u_diag = ((C)1 - k.u_axis) / (C)2;
+    k.jump_axis = (C)(scale * (2.0 / 9.0) * in.bc.delta_e);
+    k.jump_diag = (C)(scale * (1.0 / 36.0) * in.bc.delta_e);
+    return k;
+}
+
+int vec_width(int p) { return vector_width(p); }
+
+// Upload the instance table (coefficients depend on the storage scale).
+template <typename C>
+cudaError_t upload_table(lbm_batch *b) {
+    std::vector<InstDev<C>> t(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        const lbm_instance &in = b->inst[i];
+        t[i].off = b->off[i];
+        t[i].hoff = b->hoff[i];
+        t[i].plane = (long long)in.nx * in.ny;
+        t[i].nx = in.nx;
+        t[i].ny = in.ny;
+        t[i].bc_x = in.bc.x;
+        t[i].bc_y = in.bc.y;
+        t[i].k = coef_of<C>(in, b->scale);
+    }
+    cudaError_t e = cudaMemcpyAsync(b->dinst, t.data(), sizeof(InstDev<C>) * b->count,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e;
+}
+
+cudaError_t upload_table_any(lbm_batch *b) {
+    return b->precision == PREC_FP64 ? upload_table<double>(b) : upload_table<float>(b);
+}
+
+// Items and ranges of the active instances, uploaded for the next launches.
+cudaError_t rebuild_items(lbm_batch *b) {
+    const int V = vec_width(b->precision);
+    int ni = 0, nr = 0;
+    for (int i = 0; i < b->count; ++i) {
+        if (!b->active[i]) continue;
+        const long long threads = (long long)b->inst[i].nx * b->inst[i].ny / V;
+        const int begin = ni;
+        for (long long f = 0; f < threads; f += b->tpi) b->hitems[ni++] = Item{i, (int)f};
+        b->hranges[nr++] = Range{i, begin, ni};
+    }
+    b->n_items = ni;
+    b->n_ranges = nr;
+    b->hcounts[0] = ni;
+    b->hcounts[1] = nr;
+    cudaError_t e = cudaSuccess;
+    if (ni) e = cudaMemcpyAsync(b->ditems, b->hitems, sizeof(Item) * ni, cudaMemcpyHostToDevice,
+                                b->stream);
+    if (e == cudaSuccess && nr)
+        e = cudaMemcpyAsync(b->dranges, b->hranges, sizeof(Range) * nr, cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->dcounts, b->hcounts, 2 * sizeof(int), cudaMemcpyHostToDevice,
+                            b->stream);
+    // the host staging arrays are reused by the next rebuild: wait here
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e;
+}
+
+template <typename T>
+cudaError_t launch_mode(lbm_batch *b, int mode, int src, cudaStream_t s) {
+    using C = typename Store<T>::C;
+    const T *in = (const T *)b->buf[src];
+    T *out = (T *)b->buf[1 - src];
+    const auto *tab = (const InstDev<C> *)b->dinst;
+    const C inv_s = (C)(1.0 / b->scale);
+    const int hp = b->have_prev ? 1 : 0;
+    if (mode == B_STEP)
+        batch_kernel<T, B_STEP><<<b->grid, b->tpi, 0, s>>>(in, out, tab, b->ditems, b->dcounts,
+                                                          inv_s, (C *)b->hist, hp, b->partials);
+    else if (mode == B_STEP_RES)
+        batch_kernel<T, B_STEP_RES><<<b->grid, b->tpi, 0, s>>>(
+            in, out, tab, b->ditems, b->dcounts, inv_s, (C *)b->hist, hp, b->partials);
+    else
+        batch_kernel<T, B_RES_ONLY><<<b->grid, b->tpi, 0, s>>>(
+            in, out, tab, b->ditems, b->dcounts, inv_s, (C *)b->hist, hp, b->partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_any(lbm_batch *b, int mode, int src, cudaStream_t s) {
+    switch (b->precision) {
+        case PREC_FP32: return launch_mode<float>(b, mode, src, s);
+        case PREC_FP64: return launch_mode<double>(b, mode, src, s);
+        case PREC_FP16: return launch_mode<__half>(b, mode, src, s);
+        default: return launch_mode<__nv_bfloat16>(b, mode, src, s);
+    }
+}
+
+cudaError_t launch_finalize_batch(lbm_batch *b, cudaStream_t s) {
+    batch_finalize<<<b->count, 128, 0, s>>>(b->partials, b->dranges, b->dcounts + 1, b->dsums);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t occupancy(int tpi, int *per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<T, B_STEP>, tpi, 0);
+}
+
+cudaError_t plan_grid(lbm_batch *b) {
+    int per_sm = 0;
+    cudaError_t e;
+    switch (b->precision) {
+        case PREC_FP32: e = occupancy<float>(b->tpi, &per_sm); break;
+        case PREC_FP64: e = occupancy<double>(b->tpi, &per_sm); break;
+        case PREC_FP16: e = occupancy<__half>(b->tpi, &per_sm); break;
+        default: e = occupancy<__nv_bfloat16>(b->tpi, &per_sm); break;
+    }
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (b->ctas_per_sm > 0 && b->ctas_per_sm < per_sm) per_sm = b->ctas_per_sm;
+    b->grid = b->sms * per_sm;
+    return cudaSuccess;
+}
+
+void drop_graph(lbm_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_k = 0;
+}
+
+// Residual of every instance from the 5 sums (same formulas as lbm_residual).
+void finish(lbm_batch *b, int i, const double *s, double *r_out) {
+    const lbm_instance &in = b->inst[i];
+    const double n = (double)in.nx * in.ny;
+    const double mean = s[0] / n;
+    const double var_e = std::fmax(s[1] - n * mean * mean, 0.0);
+    const double denom = std::sqrt(var_e + s[2]);
+    const long k = b->steps[i] - b->prev_step[i];
+    double r = INFINITY;
+    if (b->have_prev && k > 0) {
+        const double num = std::sqrt(s[3]);
+        r = denom > 0.0 ? num / ((double)k * denom) : (num == 0.0 ? 0.0 : INFINITY);
+    }
+    if (s[4] > 0.0) r = NAN;
+    b->prev_step[i] = b->steps[i];
+    b->last_r[i] = r;
+    if (r_out) *r_out = r;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(const lbm_instance *inst, int count, lbm_precision precision,
+                            double e_ref, void *stream, lbm_batch **out) {
+    if (!out) return bfail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!inst || count < 1) return bfail(nullptr, LBM_EINVAL, "need at least one instance");
+    if (precision < LBM_FP32 || precision > LBM_FP64)
+        return bfail(nullptr, LBM_EINVAL, "unknown precision");
+    if (!std::isfinite(e_ref)) return bfail(nullptr, LBM_EINVAL, "e_ref is not finite");
+    const int V = vec_width(precision);
+    for (int i = 0; i < count; ++i) {
+        const lbm_instance &in = inst[i];
+        const std::string at = "instance " + std::to_string(i) + ": ";
+        if (in.nx < V || in.nx % V || in.ny < 1)
+            return bfail(nullptr, LBM_EINVAL,
+                         at + "nx must be a positive multiple of " + std::to_string(V));
+        if ((in.bc.x != LBM_BC_PERIODIC && in.bc.x != LBM_BC_PERIODIC_GRADIENT) ||
+            (in.bc.y != LBM_BC_PERIODIC && in.bc.y != LBM_BC_DIFFUSE_WALLS))
+            return bfail(nullptr, in.bc.x == LBM_BC_DIFFUSE_WALLS ||
+                                          in.bc.y == LBM_BC_PERIODIC_GRADIENT
+                                      ? LBM_EUNSUPPORTED
+                                      : LBM_EINVAL,
+                         at + "unsupported boundary kinds");
+        if (in.bc.y == LBM_BC_DIFFUSE_WALLS && in.ny < 2)
+            return bfail(nullptr, LBM_EINVAL, at + "walls need ny >= 2");
+        if (!std::isfinite(in.bc.delta_e)) return bfail(nullptr, LBM_EINVAL, at + "delta_e");
+        if (std::isnan(in.tau_N) || std::isnan(in.tau_R) || !(in.tau_N > 0) || !(in.tau_R > 0) ||
+            (std::isinf(in.tau_N) && std::isinf(in.tau_R)))
+            return bfail(nullptr, LBM_EINVAL, at + "tau_N and tau_R must be > 0, not both inf");
+    }
+    lbm_batch *b = new lbm_batch();
+    auto bail = [&](lbm_status s) {
+        lbm_batch_destroy(b);
+        return s;
+    };
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        return bfail(nullptr, LBM_ECUDA, "cudaGetDevice failed");
+    }
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->count = count;
+    b->precision = precision;
+    b->e_ref = e_ref;
+    b->stream = (cudaStream_t)stream;
+    b->inst.assign(inst, inst + count);
+    b->off.resize(count);
+    b->hoff.resize(count);
+    for (int i = 0; i < count; ++i) {
+        const long long n = (long long)inst[i].nx * inst[i].ny;
+        b->off[i] = b->total;
+        b->hoff[i] = b->htotal;
+        b->total += 8 * n;
+        b->htotal += 3 * n;
+        b->max_plane = std::max(b->max_plane, n);
+        b->max_items += (n / V + 127) / 128;     // items of at least 128 threads
+    }
+    b->active.assign(count, 1);
+    b->icur.assign(count, 0);
+    b->steps.assign(count, 0);
+    b->prev_step.assign(count, 0);
+    b->good.assign(count, 0);
+    b->last_r.assign(count, INFINITY);
+    const size_t es = elem_size(precision);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&b->buf[i], es * b->total);
+    if (e == cudaSuccess) e = cudaMalloc(&b->hist, csize(precision) * b->htotal);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&b->dinst, (int)precision == PREC_FP64 ? sizeof(InstDev<double>) * count
+                                                         : sizeof(InstDev<float>) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->ditems, sizeof(Item) * b->max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dranges, sizeof(Range) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dcounts, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->partials, sizeof(double) * 5 * b->max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dsums, sizeof(double) * 5 * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->fields, sizeof(double) * 3 * b->max_plane);
+    if (e == cudaSuccess) e = cudaMalloc(&b->maxbits, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->hsums, sizeof(double) * 5 * count);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->hitems, sizeof(Item) * b->max_items);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->hranges, sizeof(Range) * count);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->hcounts, 4 * sizeof(int));
+    if (e != cudaSuccess) return bail(bcuda(nullptr, e, "lbm_batch_create allocation"));
+    e = plan_grid(b);
+    if (e != cudaSuccess) return bail(bcuda(nullptr, e, "lbm_batch_create occupancy"));
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b) {
+    if (!b) return;
+    BGuard g(b->device);
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    cudaFree(b->buf[0]);
+    cudaFree(b->buf[1]);
+    cudaFree(b->hist);
+    cudaFree(b->dinst);
+    cudaFree(b->ditems);
+    cudaFree(b->dranges);
+    cudaFree(b->dcounts);
+    cudaFree(b->partials);
+    cudaFree(b->dsums);
+    cudaFree(b->fields);
+    cudaFree(b->maxbits);
+    cudaFreeHost(b->hsums);
+    cudaFreeHost(b->hitems);
+    cudaFreeHost(b->hranges);
+    cudaFreeHost(b->hcounts);
+    delete b;
+}
+
+lbm_status lbm_batch_init(lbm_batch *b, const double *e, const double *qx, const double *qy) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    BGuard g(b->device);
+    drop_graph(b);
+    // 16-bit storage: one power-of-two scale for all instances
+    b->scale = 1.0;
+    double amax = 0.0;
+    long long base = 0;
+    for (int i = 0; i < b->count; ++i) {
+        const long long n = (long long)b->inst[i].nx * b->inst[i].ny;
+        for (long long j = 0; j < n; ++j) {
+            double v = e ? (2.0 / 9.0) * std::fabs(e[base + j] - b->e_ref) : 0.0;
+            if (qx) v += std::fabs(qx[base + j]) / 3.0;
+            if (qy) v += std::fabs(qy[base + j]) / 3.0;
+            if (!std::isfinite(v)) return bfail(b, LBM_EINVAL, "initial fields are not finite");
+            amax = std::fmax(amax, v);
+        }
+        amax = std::fmax(amax, (2.0 / 9.0) * std::fabs(b->inst[i].bc.delta_e));
+        base += n;
+    }
+    if ((b->precision == PREC_FP16 || b->precision == PREC_BF16) && amax > 0.0) {
+        int ex;
+        std::frexp(amax, &ex);
+        int p = 12 - ex;
+        p = p > 100 ? 100 : (p < -100 ? -100 : p);
+        b->scale = std::ldexp(1.0, p);
+    }
+    BCK(b, upload_table_any(b));
+    base = 0;
+    for (int i = 0; i < b->count; ++i) {
+        const lbm_instance &in = b->inst[i];
+        const long long n = (long long)in.nx * in.ny;
+        double *de = b->fields, *dqx = b->fields + b->max_plane, *dqy = b->fields + 2 * b->max_plane;
+        if (e) {
+            BCK(b, cudaMemcpyAsync(de, e + base, sizeof(double) * n, cudaMemcpyHostToDevice,
+                                   b->stream));
+        } else {
+            std::vector<double> flat(n, b->e_ref);
+            BCK(b, cudaMemcpyAsync(de, flat.data(), sizeof(double) * n, cudaMemcpyHostToDevice,
+                                   b->stream));
+            BCK(b, cudaStreamSynchronize(b->stream));
+        }
+        if (qx)
+            BCK(b, cudaMemcpyAsync(dqx, qx + base, sizeof(double) * n, cudaMemcpyHostToDevice,
+                                   b->stream));
+        if (qy)
+            BCK(b, cudaMemcpyAsync(dqy, qy + base, sizeof(double) * n, cudaMemcpyHostToDevice,
+                                   b->stream));
+        cudaError_t err;
+        const long long o = b->off[i];
+        switch (b->precision) {
+            case PREC_FP32:
+                err = launch_init<float>(de, qx ? dqx : nullptr, qy ? dqy : nullptr, in.nx, in.ny,
+                                         b->e_ref, b->scale, coef_of<float>(in, b->scale),
+                                         (float *)b->buf[1] + o, (float *)b->buf[0] + o,
+                                         b->stream);
+                break;
+            case PREC_FP64:
+                err = launch_init<double>(de, qx ? dqx : nullptr, qy ? dqy : nullptr, in.nx,
+                                          in.ny, b->e_ref, b->scale,
+                                          coef_of<double>(in, b->scale),
+                                          (double *)b->buf[1] + o, (double *)b->buf[0] + o,
+                                          b->stream);
+                break;
+            case PREC_FP16:
+                err = launch_init<__half>(de, qx ? dqx : nullptr, qy ? dqy : nullptr, in.nx,
+                                          in.ny, b->e_ref, b->scale,
+                                          coef_of<float>(in, b->scale), (__half *)b->buf[1] + o,
+                                          (__half *)b->buf[0] + o, b->stream);
+                break;
+            default:
+                err = launch_init<__nv_bfloat16>(
+                    de, qx ? dqx : nullptr, qy ? dqy : nullptr, in.nx, in.ny, b->e_ref, b->scale,
+                    coef_of<float>(in, b->scale), (__nv_bfloat16 *)b->buf[1] + o,
+                    (__nv_bfloat16 *)b->buf[0] + o, b->stream);
+        }
+        if (err != cudaSuccess) return bcuda(b, err, "batch init kernel");
+        BCK(b, cudaStreamSynchronize(b->stream));   // staging reused by the next instance
+        base += n;
+    }
+    // no history yet: zero it so the first comparison reads defined values
+    BCK(b, cudaMemsetAsync(b->hist, 0, csize(b->precision) * b->htotal, b->stream));
+    b->cur = 0;
+    b->initialised = true;
+    b->have_prev = false;
+    std::fill(b->active.begin(), b->active.end(), 1);
+    std::fill(b->icur.begin(), b->icur.end(), 0);
+    std::fill(b->steps.begin(), b->steps.end(), 0);
+    std::fill(b->prev_step.begin(), b->prev_step.end(), 0);
+    std::fill(b->good.begin(), b->good.end(), 0);
+    std::fill(b->last_r.begin(), b->last_r.end(), INFINITY);
+    BCK(b, rebuild_items(b));
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, long n) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (n < 0) return bfail(b, LBM_EINVAL, "n must be >= 0");
+    if (!b->initialised) return bfail(b, LBM_EINVAL, "lbm_batch_init has not been called");
+    BGuard g(b->device);
+    for (long s = 0; s < n; ++s) {
+        BCK(b, launch_any(b, B_STEP, b->cur, b->stream));
+        b->cur = 1 - b->cur;
+    }
+    for (int i = 0; i < b->count; ++i)
+        if (b->active[i]) {
+            b->steps[i] += n;
+            b->icur[i] = b->cur;
+        }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_residuals(lbm_batch *b, double *r, double *energy) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (!b->initialised) return bfail(b, LBM_EINVAL, "lbm_batch_init has not been called");
+    BGuard g(b->device);
+    bool any_zero = false;
+    for (int i = 0; i < b->count; ++i) any_zero |= b->active[i] && b->steps[i] == 0;
+    if (any_zero)
+        return bfail(b, LBM_EUNSUPPORTED, "residuals need at least one step since init");
+    // read-only pass over the state of every active instance (pulled from
+    // the buffer read last)
+    BCK(b, launch_any(b, B_RES_ONLY, 1 - b->cur, b->stream));
+    BCK(b, launch_finalize_batch(b, b->stream));
+    BCK(b, cudaMemcpyAsync(b->hsums, b->dsums, sizeof(double) * 5 * b->count,
+                           cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    bool bad = false;
+    for (int i = 0; i < b->count; ++i) {
+        if (!b->active[i]) continue;
+        const double *s = b->hsums + 5 * i;
+        finish(b, i, s, nullptr);
+        const double n = (double)b->inst[i].nx * b->inst[i].ny;
+        if (energy) energy[i] = n * b->e_ref + s[0];
+        bad |= s[4] > 0.0;
+    }
+    b->have_prev = true;
+    if (r)
+        for (int i = 0; i < b->count; ++i) r[i] = b->last_r[i];
+    if (bad) return bfail(b, LBM_ENONFINITE, "an instance holds NaN or Inf");
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_solve(lbm_batch *b, double tol, int check_every, long max_steps,
+                           long *steps, double *r) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (!b->initialised) return bfail(b, LBM_EINVAL, "lbm_batch_init has not been called");
+    if (!(tol > 0.0)) return bfail(b, LBM_EINVAL, "tol must be > 0");
+    if (check_every < 2 || (check_every & 1))
+        return bfail(b, LBM_EINVAL, "check_every must be an even number >= 2");
+    if (max_steps < 0) return bfail(b, LBM_EINVAL, "max_steps must be >= 0");
+    BGuard g(b->device);
+    // a window has an even number of steps, so it ends on the buffer parity
+    // it started with; the graph is captured for the current parity
+    if (!b->graph || b->graph_k != check_every || b->graph_parity != b->cur) {
+        drop_graph(b);
+        cudaStream_t cap = nullptr;
+        BCK(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int src = b->cur;
+        for (int s = 0; s < check_every - 1 && e == cudaSuccess; ++s, src = 1 - src)
+            e = launch_any(b, B_STEP, src, cap);
+        // have_prev is a launch argument: capture the comparing variant;
+        // the first window's comparison is ignored (no history yet)
+        const bool hp = b->have_prev;
+        b->have_prev = true;
+        if (e == cudaSuccess) e = launch_any(b, B_STEP_RES, src, cap);
+        b->have_prev = hp;
+        if (e == cudaSuccess) e = launch_finalize_batch(b, cap);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->hsums, b->dsums, sizeof(double) * 5 * b->count,
+                                cudaMemcpyDeviceToHost, cap);
+        cudaGraph_t gr = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(cap, &gr);
+        cudaStreamDestroy(cap);
+        if (e == cudaSuccess) e = ee;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return bcuda(b, e, "batch window capture");
+        }
+        b->graph_k = check_every;
+        b->graph_parity = b->cur;
+    }
+    bool bad = false;
+    while (true) {
+        bool any = false;
+        for (int i = 0; i < b->count; ++i) any |= b->active[i] && b->steps[i] < max_steps;
+        if (!any) break;
+        // instances that reached max_steps stop too
+        bool changed = false;
+        for (int i = 0; i < b->count; ++i)
+            if (b->active[i] && b->steps[i] >= max_steps) {
+                b->active[i] = 0;
+                changed = true;
+            }
+        if (changed) BCK(b, rebuild_items(b));
+        BCK(b, cudaGraphLaunch(b->graph, b->stream));
+        BCK(b, cudaStreamSynchronize(b->stream));
+        changed = false;
+        for (int i = 0; i < b->count; ++i) {
+            if (!b->active[i]) continue;
+            b->steps[i] += check_every;
+            b->icur[i] = b->cur;
+            double ri;
+            finish(b, i, b->hsums + 5 * i, &ri);
+            if (std::isnan(ri)) {
+                bad = true;
+                b->active[i] = 0;
+                changed = true;
+                continue;
+            }
+            b->good[i] = b->last_r[i] < tol ? b->good[i] + 1 : 0;
+            if (b->good[i] >= 2) {
+                b->active[i] = 0;          // steady: retire
+                changed = true;
+            }
+        }
+        b->have_prev = true;
+        if (changed) BCK(b, rebuild_items(b));
+    }
+    for (int i = 0; i < b->count; ++i) {
+        if (steps) steps[i] = b->steps[i];
+        if (r) r[i] = b->last_r[i];
+    }
+    if (bad) return bfail(b, LBM_ENONFINITE, "an instance became non-finite (retired)");
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_moments(lbm_batch *b, int i, double *e, double *qx, double *qy) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (i < 0 || i >= b->count) return bfail(b, LBM_EINVAL, "instance index out of range");
+    if (!b->initialised) return bfail(b, LBM_EINVAL, "lbm_batch_init has not been called");
+    BGuard g(b->device);
+    const lbm_instance &in = b->inst[i];
+    const long long n = (long long)in.nx * in.ny;
+    const Params p = params_of(in);
+    Readout rd;
+    rd.nx = in.nx;
+    rd.ny = in.ny;
+    rd.bc_x = in.bc.x;
+    rd.bc_y = in.bc.y;
+    rd.pulled = b->steps[i] > 0;
+    rd.e_ref = b->e_ref;
+    rd.inv_scale = 1.0 / b->scale;
+    rd.kappa = p.kappa;
+    double *d[3] = {b->fields, b->fields + b->max_plane, b->fields + 2 * b->max_plane};
+    const long long o = b->off[i];
+    const int src = 1 - b->icur[i];      // the buffer this instance read last
+    cudaError_t err;
+    switch (b->precision) {
+        case PREC_FP32:
+            err = launch_moments<float>((const float *)b->buf[src] + o, rd,
+                                        coef_of<float>(in, b->scale), d[0], d[1], d[2],
+                                        b->stream);
+            break;
+        case PREC_FP64:
+            err = launch_moments<double>((const double *)b->buf[src] + o, rd,
+                                         coef_of<double>(in, b->scale), d[0], d[1], d[2],
+                                         b->stream);
+            break;
+        case PREC_FP16:
+            err = launch_moments<__half>((const __half *)b->buf[src] + o, rd,
+                                         coef_of<float>(in, b->scale), d[0], d[1], d[2],
+                                         b->stream);
+            break;
+        default:
+            err = launch_moments<__nv_bfloat16>((const __nv_bfloat16 *)b->buf[src] + o, rd,
+                                                coef_of<float>(in, b->scale), d[0], d[1], d[2],
+                                                b->stream);
+    }
+    if (err != cudaSuccess) return bcuda(b, err, "batch moments");
+    double *h[3] = {e, qx, qy};
+    for (int f = 0; f < 3; ++f)
+        if (h[f])
+            BCK(b, cudaMemcpyAsync(h[f], d[f], sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                   b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_schedule(lbm_batch *b, int threads_per_item, int ctas_per_sm) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (threads_per_item != 128 && threads_per_item != 256 && threads_per_item != 512)
+        return bfail(b, LBM_EINVAL, "threads_per_item must be 128, 256 or 512");
+    if (ctas_per_sm < 0) return bfail(b, LBM_EINVAL, "ctas_per_sm must be >= 0");
+    BGuard g(b->device);
+    const int old_t = b->tpi, old_c = b->ctas_per_sm;
+    b->tpi = threads_per_item;
+    b->ctas_per_sm = ctas_per_sm;
+    cudaError_t e = plan_grid(b);
+    if (e != cudaSuccess) {
+        b->tpi = old_t;
+        b->ctas_per_sm = old_c;
+        plan_grid(b);
+        return bcuda(b, e, "batch schedule");
+    }
+    drop_graph(b);
+    if (b->initialised) BCK(b, rebuild_items(b));
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_schedule(const lbm_batch *b, int *threads_per_item, int *ctas_per_sm,
+                                  int *grid) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (threads_per_item) *threads_per_item = b->tpi;
+    if (ctas_per_sm) *ctas_per_sm = b->grid / (b->sms > 0 ? b->sms : 1);
+    if (grid) *grid = b->grid;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, double *us_per_step) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (!b->initialised) return bfail(b, LBM_EINVAL, "lbm_batch_init has not been called");
+    if (trial_steps < 0) return bfail(b, LBM_EINVAL, "trial_steps must be >= 0");
+    if (trial_steps == 0) trial_steps = 10;
+    if (trial_steps & 1) ++trial_steps;
+    BGuard g(b->device);
+    // timings run on the live buffers: keep a copy of the state
+    const size_t bytes = elem_size(b->precision) * b->total;
+    void *saved = nullptr;
+    BCK(b, cudaMallocAsync(&saved, 2 * bytes, b->stream));
+    for (int i = 0; i < 2; ++i)
+        BCK(b, cudaMemcpyAsync((char *)saved + i * bytes, b->buf[i], bytes,
+                               cudaMemcpyDeviceToDevice, b->stream));
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    const int old_t = b->tpi, old_c = b->ctas_per_sm;
+    float best = -1.f;
+    int best_t = old_t, best_c = old_c;
+    cudaError_t err = cudaSuccess;
+    for (int tpi : {128, 256, 512}) {
+        for (int cps : {0, 1, 2}) {
+            b->tpi = tpi;
+            b->ctas_per_sm = cps;
+            if (plan_grid(b) != cudaSuccess) {
+                (void)cudaGetLastError();
+                continue;
+            }
+            if ((err = rebuild_items(b)) != cudaSuccess) break;
+            for (int s = 0; s < 2 && err == cudaSuccess; ++s)
+                err = launch_any(b, B_STEP, s & 1, b->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+            for (int s = 0; s < trial_steps && err == cudaSuccess; ++s)
+                err = launch_any(b, B_STEP, s & 1, b->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err != cudaSuccess) break;
+            if (best < 0.f || ms < best) {
+                best = ms;
+                best_t = tpi;
+                best_c = cps;
+            }
+        }
+        if (err != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < 2 && err == cudaSuccess; ++i)
+        err = cudaMemcpyAsync(b->buf[i], (char *)saved + i * bytes, bytes,
+                              cudaMemcpyDeviceToDevice, b->stream);
+    cudaFreeAsync(saved, b->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(b->stream);
+    b->tpi = best_t;
+    b->ctas_per_sm = best_c;
+    cudaError_t pe = plan_grid(b);
+    drop_graph(b);
+    if (err == cudaSuccess) err = pe;
+    if (err == cudaSuccess) err = rebuild_items(b);
+    if (err != cudaSuccess) return bcuda(b, err, "lbm_batch_autotune");
+    if (us_per_step) *us_per_step = best >= 0.f ? 1000.0 * best / trial_steps : 0.0;
+    return LBM_OK;
+}
+
+long lbm_batch_active(const lbm_batch *b) {
+    if (!b) return -1;
+    long n = 0;
+    for (char a : b->active) n += a ? 1 : 0;
+    return n;
+}
+
+long lbm_batch_steps(const lbm_batch *b, int i) {
+    if (!b || i < 0 || i >= b->count) return -1;
+    return b->steps[i];
+}
+
+const char *lbm_batch_last_error(const lbm_batch *b) {
+    if (!b) return "batch is NULL";
+    return b->err.c_str();
+}
+
+}  // extern "C"

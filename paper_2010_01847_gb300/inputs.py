@@ -124,3 +124,19 @@ def initial_fields(w: Workload):
         raise KeyError(w.name)
     z = np.zeros_like(e)
     return e, z, z.copy()
+
+
+def batch_channels(count: int, seed: int = SEED, w_range=(16, 512),
+                   kn_N_range=(1e-3, 1e-1), kn_R_range=(0.1, 10.0)):
+    """Candidate phonon-Poiseuille channels for the batched workload: width W
+    uniform in w_range (integers), length 4W, Kn_N and Kn_R log-uniform,
+    seeded.  Returns a list of dicts (W, nx=4W, ny=W, kn_N, kn_R, d=W-1);
+    the caller decides which candidates it keeps."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        W = int(rng.integers(w_range[0], w_range[1] + 1))
+        kn_N = float(10 ** rng.uniform(np.log10(kn_N_range[0]), np.log10(kn_N_range[1])))
+        kn_R = float(10 ** rng.uniform(np.log10(kn_R_range[0]), np.log10(kn_R_range[1])))
+        out.append({"W": W, "nx": 4 * W, "ny": W, "kn_N": kn_N, "kn_R": kn_R, "d": W - 1})
+    return out

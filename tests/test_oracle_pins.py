@@ -319,3 +319,34 @@ def test_thread_count_does_not_change_results():
         runs.append(lat.f.copy())
     oracle.set_threads(1)
     assert np.array_equal(runs[0], runs[1])
+
+
+# --- linear stability of the scheme near tau -> 1/2 ---------------------------
+def test_instability_below_tau_bound_matches_mode_matrix():
+    """The D2Q8 scheme without a rest population is linearly unstable for
+    tau below ~0.576 (tau_r = inf): the exact mode matrix has spectral radius
+    > 1 near k = (2.06, pi).  The looped oracle must grow at exactly the rate
+    the matrix predicts (64 x 2 lattice: k = 2 pi 21/64 and pi are on it), and
+    stay bounded just above the bound."""
+    nx, ny = 64, 2
+    kx, ky = 2 * np.pi * 21 / nx, np.pi
+    for tau, grows in ((0.55, True), (0.6, False)):
+        tau_N = tau - 0.5
+        Mk = um.mode_matrix(kx, ky, tau, math.inf)
+        rho = np.abs(np.linalg.eigvals(Mk)).max()
+        assert (rho > 1 + 1e-6) == grows
+        e = 1 + 1e-6 * inputs.uniform_noise((ny, nx), 1.0, seed=3)
+        lat = oracle.run(nx, ny, tau_N, math.inf, e)
+        lat.step(400)
+        a = np.linalg.norm(lat.f - oracle.OMEGA)
+        lat.step(200)
+        b = np.linalg.norm(lat.f - oracle.OMEGA)
+        if grows:
+            # the largest growing mode on this lattice dominates after 400
+            # steps; its complex eigenvalue makes the norm oscillate slightly
+            rates = [np.abs(np.linalg.eigvals(um.mode_matrix(2 * np.pi * m / nx, np.pi * j, tau,
+                                                               math.inf))).max()
+                     for m in range(nx) for j in (0, 1)]
+            assert (b / a) ** (1 / 200) == pytest.approx(max(rates), rel=1e-4)
+        else:
+            assert b <= 1e-5
