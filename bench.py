@@ -63,6 +63,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="heat_mode", choices=["heat_mode", "batch"],
+                    help="heat_mode: 8192^2 throughput (default); batch: 512 channels "
+                         "solved to steady state")
+    ap.add_argument("--instances", type=int, default=512)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-steps", type=int, default=400000)
+    ap.add_argument("--sequential-sample", type=int, default=16)
     return ap.parse_args()
 
 
@@ -401,10 +408,96 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def batch_instances(n, seed=inputs.SEED):
+    """The batched-channel workload: seeded candidates (width W in [16, 512],
+    length 4W, Kn_N log-U[1e-3, 1e-1], Kn_R log-U[0.1, 10], walls, periodic
+    temperature gradient with delta_e = 1e-3) whose tau is at least 0.6, the
+    scheme's linear-stability bound with margin; returns (kept, rejected)."""
+    import paper_2010_01847_gb300 as plbm
+    kept, rejected = [], 0
+    for c in inputs.batch_channels(8 * n, seed=seed):
+        tau_N = plbm.tau_from_kn(c["kn_N"], c["d"])
+        tau_R = plbm.tau_from_kn(c["kn_R"], c["d"])
+        tau = 1.0 / (1.0 / tau_N + 1.0 / tau_R) + 0.5
+        if tau < 0.6:
+            rejected += 1
+            continue
+        kept.append(dict(nx=c["nx"], ny=c["ny"], tau_N=tau_N, tau_R=tau_R,
+                         bc_x=inputs.PERIODIC_GRADIENT, bc_y=inputs.WALLS, delta_e=1e-3,
+                         W=c["W"], kn_N=c["kn_N"], kn_R=c["kn_R"]))
+        if len(kept) == n:
+            break
+    return kept, rejected
+
+
+def run_batch(args):
+    """Time to steady state (r < tol on two consecutive checks every 100
+    steps) of the batched channels from a cold start (e = 1, q = 0), with
+    the plain single-lattice solver on a sample of them as the baseline."""
+    import torch
+    import paper_2010_01847_gb300 as plbm
+    torch.cuda.set_device(0)
+    inst, rejected = batch_instances(args.instances)
+    sites = np.array([i["nx"] * i["ny"] for i in inst], dtype=np.float64)
+    b = plbm.Batch(inst)
+    b.init()
+    tune_us = b.autotune(10)
+    b.init()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, r = b.solve(args.tol, 100, args.max_steps)
+    t_batch = time.perf_counter() - t0
+    updates = float((steps * sites).sum())
+    # plain solver, one lattice at a time, on a seeded sample
+    rng = np.random.default_rng(5)
+    sample = sorted(rng.choice(len(inst), size=min(args.sequential_sample, len(inst)),
+                               replace=False).tolist())
+    t_seq = 0.0
+    seq_updates = 0.0
+    for k in sample:
+        i = inst[k]
+        lat = plbm.Lattice(i["nx"], i["ny"], i["tau_N"], i["tau_R"], i["bc_x"], i["bc_y"],
+                           i["delta_e"])
+        lat.init(np.ones((i["ny"], i["nx"])))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lat.residual()
+        good, n = 0, 0
+        while n < args.max_steps:
+            rr, _ = lat.step_residual(100)
+            n += 100
+            good = good + 1 if rr < args.tol else 0
+            if good >= 2:
+                break
+        t_seq += time.perf_counter() - t1
+        seq_updates += n * i["nx"] * i["ny"]
+        lat.close()
+    sample_batch_updates = float((steps[sample] * sites[sample]).sum())
+    line = {
+        "metric": "time to steady state (r < 1e-8), batched channels, cold start",
+        "value": t_batch, "unit": "s", "n_gpus": 1, "higher_is_better": False,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched_channels_{len(inst)}", "instances": len(inst),
+                   "rejected_unstable_candidates": rejected,
+                   "total_sites": int(sites.sum()), "tol": args.tol, "check_every": 100,
+                   "schedule": b.schedule, "autotune_us_per_step": tune_us},
+        "steps": {"min": int(steps.min()), "median": float(np.median(steps)),
+                  "max": int(steps.max()), "all_converged": bool(np.all(r < args.tol))},
+        "site_updates": updates, "glups": updates / t_batch / 1e9,
+        "plain_sequential_sample": {
+            "instances": len(sample), "seconds": t_seq, "site_updates": seq_updates,
+            "glups": seq_updates / t_seq / 1e9,
+            "estimated_seconds_all": t_seq * updates / max(seq_updates, 1.0)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_native(args)
 

@@ -315,6 +315,24 @@ lbm_status lbm_batch_get_schedule(const lbm_batch *batch, int *threads_per_item,
  * Synchronous. */
 lbm_status lbm_batch_autotune(lbm_batch *batch, int trial_steps, double *us_per_step);
 
+/* Normalised steady profiles of every instance (all need the periodic
+ * temperature gradient with delta_e != 0 and a finite tau_R), into a DEVICE
+ * float array [count][512]: entries 0..255 are Q(Y) = q_x / q_F at
+ * Y = j/255 across the channel (row means, linear interpolation), with the
+ * Fourier flux q_F = (5/9) tau_R delta_e / nx (Eqs. 59-60 fix the slope
+ * |de/dx| = delta_e / nx); entries 256..511 are E(Y) = (row mean of
+ * e + delta_e (x - (nx-1)/2) / nx - e_ref) / delta_e.  Synchronous. */
+lbm_status lbm_batch_profiles(lbm_batch *batch, float *out);
+
+/* Step 0 of every instance from DEVICE profiles in the layout of
+ * lbm_batch_profiles (the learned warm start): q_x = Q(Y) q_F, q_y = 0,
+ * e = e_ref + delta_e (E(Y) - <E> - (x - (nx-1)/2) / nx), then Eq. 15, where
+ * <E> is the row mean of E: a channel conserves its total energy, so the
+ * start keeps the cold start's mean energy and reaches the same steady
+ * state.  FP32 or FP64 storage.  Resets steps, history and retirement.
+ * Synchronous. */
+lbm_status lbm_batch_init_profiles(lbm_batch *batch, const float *profiles);
+
 /* Running (not retired) instances, and the steps instance i has run. */
 long lbm_batch_active(const lbm_batch *batch);
 long lbm_batch_steps(const lbm_batch *batch, int i);
@@ -322,6 +340,40 @@ long lbm_batch_steps(const lbm_batch *batch, int i);
 /* Text of the batch's last failure (of the last failed lbm_batch_create via
  * lbm_last_error(NULL)). */
 const char *lbm_batch_last_error(const lbm_batch *batch);
+
+/* ---- Warm-start network ---------------------------------------------------
+ * A multilayer perceptron trained on the GPU to map a channel's parameters
+ * to its steady profile (the layout of lbm_batch_profiles), so a solve can
+ * start near steady state.  Layer l: Z = X W_l^T + b_l with W_l stored
+ * [width_{l+1}][width_l] row-major; GELU (x Phi(x)) after every layer but
+ * the last.  Products take BF16 operands on the tensor cores with FP32
+ * accumulation; parameters, gradients and Adam moments are FP32.  The
+ * paper has no network: this is the build's warm-start extension. */
+typedef struct lbm_mlp lbm_mlp;
+
+/* widths[0] inputs, widths[n_widths-1] outputs; max_batch rows per call. */
+lbm_status lbm_mlp_create(const int *widths, int n_widths, int max_batch, void *stream,
+                          lbm_mlp **out);
+void lbm_mlp_destroy(lbm_mlp *mlp);
+/* Number of FP32 parameters: per layer W_l (row-major) then b_l. */
+size_t lbm_mlp_param_count(const lbm_mlp *mlp);
+/* Copy parameters from / to HOST (FP32, the layout above); setting them
+ * clears the Adam moments.  Synchronous. */
+lbm_status lbm_mlp_set_params(lbm_mlp *mlp, const float *host);
+lbm_status lbm_mlp_get_params(lbm_mlp *mlp, float *host);
+/* y = network(x) for `batch` rows: DEVICE float x [batch][in], y [batch][out].
+ * Async. */
+lbm_status lbm_mlp_forward(lbm_mlp *mlp, const float *x, int batch, float *y);
+/* Mean squared error against DEVICE targets t and, if grads is not NULL, its
+ * gradient with respect to every parameter into HOST memory (param_count
+ * floats).  Synchronous. */
+lbm_status lbm_mlp_loss_grad(lbm_mlp *mlp, const float *x, const float *t, int batch,
+                             double *loss, float *grads);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error;
+ * *loss is the loss before the update.  Synchronous. */
+lbm_status lbm_mlp_train_step(lbm_mlp *mlp, const float *x, const float *t, int batch,
+                              float lr, double *loss);
+const char *lbm_mlp_last_error(const lbm_mlp *mlp);
 
 /* ---- Residual without device allocation ---------------------------------
  * The paper has no counterpart to this call; it serves callers that must not

@@ -43,7 +43,10 @@ EXPORTS = [
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_init", "lbm_batch_step",
     "lbm_batch_residuals", "lbm_batch_solve", "lbm_batch_moments", "lbm_batch_set_schedule",
     "lbm_batch_get_schedule", "lbm_batch_autotune", "lbm_batch_active", "lbm_batch_steps",
-    "lbm_batch_last_error",
+    "lbm_batch_last_error", "lbm_batch_profiles", "lbm_batch_init_profiles",
+    "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_param_count", "lbm_mlp_set_params",
+    "lbm_mlp_get_params", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train_step",
+    "lbm_mlp_last_error",
     "lbm_residual_noalloc",
 ]
 NOALLOC_MAX_NODES = 16777216
@@ -130,6 +133,18 @@ def load_library(path: str = LIB_PATH):
         "lbm_batch_active": (c_long, [vp]),
         "lbm_batch_steps": (c_long, [vp, ctypes.c_int]),
         "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_batch_profiles": (st, [vp, vp]),
+        "lbm_batch_init_profiles": (st, [vp, vp]),
+        "lbm_mlp_create": (st, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, vp,
+                                ctypes.POINTER(vp)]),
+        "lbm_mlp_destroy": (None, [vp]),
+        "lbm_mlp_param_count": (c_size, [vp]),
+        "lbm_mlp_set_params": (st, [vp, vp]),
+        "lbm_mlp_get_params": (st, [vp, vp]),
+        "lbm_mlp_forward": (st, [vp, vp, ctypes.c_int, vp]),
+        "lbm_mlp_loss_grad": (st, [vp, vp, vp, ctypes.c_int, dp, vp]),
+        "lbm_mlp_train_step": (st, [vp, vp, vp, ctypes.c_int, ctypes.c_float, dp]),
+        "lbm_mlp_last_error": (ctypes.c_char_p, [vp]),
         "lbm_residual_noalloc": (st, [vp, vp, vp, vp, vp, vp, ctypes.c_longlong,
                                       ctypes.c_double, c_long, vp, dp, dp]),
     }
@@ -477,9 +492,112 @@ class Batch:
         self._check(self._lib.lbm_batch_autotune(self._b, int(trial_steps), ctypes.byref(us)))
         return us.value
 
+    def profiles(self):
+        """Normalised steady profiles [count, 512] (CUDA float32 tensor)."""
+        out = self.torch.empty((self.count, 512), dtype=self.torch.float32, device="cuda")
+        self._check(self._lib.lbm_batch_profiles(self._b, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def init_profiles(self, profiles):
+        """Step 0 from predicted profiles [count, 512] (CUDA float32)."""
+        p = profiles.to(device="cuda", dtype=self.torch.float32).contiguous()
+        assert p.shape == (self.count, 512)
+        self._check(self._lib.lbm_batch_init_profiles(self._b, ctypes.c_void_p(p.data_ptr())))
+
     @property
     def active(self):
         return self._lib.lbm_batch_active(self._b)
 
     def steps_of(self, i):
         return self._lib.lbm_batch_steps(self._b, int(i))
+
+
+class Mlp:
+    """The warm-start network (see lbm_mlp_* in include/phonon_lbm.h)."""
+
+    def __init__(self, widths, max_batch=4096):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the network runs only on the GPU")
+        self._lib = load_library()
+        self.torch = torch
+        self.widths = [int(w) for w in widths]
+        arr = (ctypes.c_int * len(self.widths))(*self.widths)
+        self.stream = torch.cuda.current_stream()
+        self._m = ctypes.c_void_p()
+        st = self._lib.lbm_mlp_create(arr, len(self.widths), int(max_batch),
+                                      ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.byref(self._m))
+        if st != OK:
+            self._m = ctypes.c_void_p()
+            raise LBMError(st, self._lib.lbm_last_error(None).decode())
+        self.max_batch = int(max_batch)
+
+    def _check(self, st):
+        if st != OK:
+            raise LBMError(st, self._lib.lbm_mlp_last_error(self._m).decode())
+
+    def close(self):
+        if self._m:
+            self._lib.lbm_mlp_destroy(self._m)
+            self._m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def param_count(self):
+        return self._lib.lbm_mlp_param_count(self._m)
+
+    def init_params(self, seed=0):
+        """Seeded uniform(-a, a) weights, a = sqrt(6 / (fan_in + fan_out)),
+        zero biases."""
+        rng = np.random.default_rng(seed)
+        parts = []
+        for k, n in zip(self.widths[:-1], self.widths[1:]):
+            a = np.sqrt(6.0 / (k + n))
+            parts += [rng.uniform(-a, a, n * k), np.zeros(n)]
+        self.set_params(np.concatenate(parts).astype(np.float32))
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.param_count
+        self._check(self._lib.lbm_mlp_set_params(self._m, p.ctypes.data_as(ctypes.c_void_p)))
+
+    def params(self):
+        p = np.empty(self.param_count, dtype=np.float32)
+        self._check(self._lib.lbm_mlp_get_params(self._m, p.ctypes.data_as(ctypes.c_void_p)))
+        return p
+
+    def _dev(self, a):
+        t = self.torch.as_tensor(a, dtype=self.torch.float32, device="cuda")
+        return t.contiguous()
+
+    def forward(self, x):
+        x = self._dev(x)
+        y = self.torch.empty((x.shape[0], self.widths[-1]), dtype=self.torch.float32,
+                             device="cuda")
+        self._check(self._lib.lbm_mlp_forward(self._m, ctypes.c_void_p(x.data_ptr()),
+                                              x.shape[0], ctypes.c_void_p(y.data_ptr())))
+        return y
+
+    def loss_grad(self, x, t):
+        x, t = self._dev(x), self._dev(t)
+        g = np.empty(self.param_count, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self._lib.lbm_mlp_loss_grad(self._m, ctypes.c_void_p(x.data_ptr()),
+                                                ctypes.c_void_p(t.data_ptr()), x.shape[0],
+                                                ctypes.byref(loss),
+                                                g.ctypes.data_as(ctypes.c_void_p)))
+        return loss.value, g
+
+    def train_step(self, x, t, lr):
+        x, t = self._dev(x), self._dev(t)
+        loss = ctypes.c_double()
+        self._check(self._lib.lbm_mlp_train_step(self._m, ctypes.c_void_p(x.data_ptr()),
+                                                 ctypes.c_void_p(t.data_ptr()), x.shape[0],
+                                                 ctypes.c_float(lr), ctypes.byref(loss)))
+        return loss.value

@@ -139,6 +139,86 @@ batch_finalize(const double *__restrict__ partials, const Range *__restrict__ ra
     block_sum5_store(acc, sums + (size_t)r.inst * 5);
 }
 
+// Normalised steady profiles of one channel instance from its moment fields
+// (device doubles [ny][nx]): for output point j of P = 256 at Y = j/(P-1),
+// linear interpolation between rows y0 and y0 + 1 of the row means of
+//   Q = q_x nx / ((5/9) tau_R delta_e)     (heat flux over the Fourier flux)
+//   E = (e + delta_e (x - (nx-1)/2) / nx - e_ref) / delta_e   (e minus its
+//        x-affine part).
+// One block per output point; out[0..P) = Q, out[P..2P) = E.
+constexpr int PROFILE_POINTS = 256;
+
+__global__ void __launch_bounds__(128)
+channel_profile(const double *__restrict__ e, const double *__restrict__ qx, int nx, int ny,
+                double e_ref, double delta_e, double q_unit, float *__restrict__ out) {
+    const int j = blockIdx.x;
+    const double yf = (double)j / (PROFILE_POINTS - 1) * (ny - 1);
+    int y0 = (int)floor(yf);
+    if (y0 > ny - 1) y0 = ny - 1;
+    const int y1 = y0 + 1 < ny ? y0 + 1 : y0;
+    const double w = yf - y0;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        const double aff = delta_e * ((double)x - 0.5 * (nx - 1)) / nx;
+        acc[0] += qx[(long long)y0 * nx + x];
+        acc[1] += qx[(long long)y1 * nx + x];
+        acc[2] += e[(long long)y0 * nx + x] + aff - e_ref;
+        acc[3] += e[(long long)y1 * nx + x] + aff - e_ref;
+    }
+    __shared__ double res[5];
+    block_sum5_store(acc, res);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double q = ((1.0 - w) * res[0] + w * res[1]) / nx;
+        const double ed = ((1.0 - w) * res[2] + w * res[3]) / nx;
+        out[j] = (float)(q / q_unit);
+        out[PROFILE_POINTS + j] = (float)(ed / delta_e);
+    }
+}
+
+// Interpolated value of a 256-point profile at row y of ny.
+__device__ __forceinline__ double profile_at(const float *__restrict__ p, int y, int ny) {
+    const double t = ny > 1 ? (double)y / (ny - 1) * (PROFILE_POINTS - 1) : 0.0;
+    int j0 = (int)floor(t);
+    if (j0 > PROFILE_POINTS - 2) j0 = PROFILE_POINTS - 2;
+    const double w = t - j0;
+    return (1.0 - w) * p[j0] + w * p[j0 + 1];
+}
+
+// Mean over the ny rows of the interpolated E profile (one block).  The
+// channel conserves its total energy, so the steady state keeps the starting
+// mean; removing this mean makes a profile start reach the same steady
+// state as the cold start e = e_ref.
+__global__ void __launch_bounds__(128)
+profile_e_mean(const float *__restrict__ prof, int ny, double *__restrict__ out) {
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int y = threadIdx.x; y < ny; y += blockDim.x)
+        acc[0] += profile_at(prof + PROFILE_POINTS, y, ny);
+    __shared__ double res[5];
+    block_sum5_store(acc, res);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = res[0] / ny;
+}
+
+// Initial fields of one channel from its predicted profile (same
+// normalisation as channel_profile): q_x = Q(Y) q_unit, q_y = 0,
+// e = e_ref + delta_e (E(Y) - mean E - (x - (nx-1)/2) / nx), Y = y/(ny-1).
+__global__ void channel_fields(const float *__restrict__ prof, int nx, int ny, double e_ref,
+                               double delta_e, double q_unit, const double *__restrict__ e_mean,
+                               double *__restrict__ e, double *__restrict__ qx,
+                               double *__restrict__ qy) {
+    const long long n = (long long)nx * ny;
+    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < n;
+         node += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(node / nx), x = (int)(node - (long long)y * nx);
+        const double Q = profile_at(prof, y, ny);
+        const double E = profile_at(prof + PROFILE_POINTS, y, ny) - *e_mean;
+        e[node] = e_ref + delta_e * (E - ((double)x - 0.5 * (nx - 1)) / nx);
+        qx[node] = Q * q_unit;
+        qy[node] = 0.0;
+    }
+}
+
 }  // namespace
 }  // namespace plbm
 
@@ -895,6 +975,130 @@ long lbm_batch_active(const lbm_batch *b) {
 long lbm_batch_steps(const lbm_batch *b, int i) {
     if (!b || i < 0 || i >= b->count) return -1;
     return b->steps[i];
+}
+
+// Heat-flux unit of a channel's normalised profile: (5/9) tau_R delta_e / nx,
+// i.e. the Fourier flux (1/3) C_V v_g^2 tau_R |dT/dx| in lattice units with
+// the steady slope |de/dx| = delta_e / nx of Eqs. 59-60.
+static double q_unit_of(const lbm_instance &in) {
+    return (5.0 / 9.0) * in.tau_R * in.bc.delta_e / in.nx;
+}
+
+static bool profile_ok(const lbm_instance &in) {
+    return in.bc.x == LBM_BC_PERIODIC_GRADIENT && in.bc.delta_e != 0.0 &&
+           std::isfinite(in.tau_R);
+}
+
+lbm_status lbm_batch_profiles(lbm_batch *b, float *out) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (!out) return bfail(b, LBM_EINVAL, "out is NULL");
+    if (!b->initialised) return bfail(b, LBM_EINVAL, "lbm_batch_init has not been called");
+    for (int i = 0; i < b->count; ++i)
+        if (!profile_ok(b->inst[i]))
+            return bfail(b, LBM_EUNSUPPORTED,
+                         "instance " + std::to_string(i) +
+                             ": profiles need the periodic temperature gradient (delta_e != 0) "
+                             "and finite tau_R");
+    BGuard g(b->device);
+    for (int i = 0; i < b->count; ++i) {
+        const lbm_instance &in = b->inst[i];
+        const Params p = params_of(in);
+        Readout rd;
+        rd.nx = in.nx;
+        rd.ny = in.ny;
+        rd.bc_x = in.bc.x;
+        rd.bc_y = in.bc.y;
+        rd.pulled = b->steps[i] > 0;
+        rd.e_ref = b->e_ref;
+        rd.inv_scale = 1.0 / b->scale;
+        rd.kappa = p.kappa;
+        double *d[3] = {b->fields, b->fields + b->max_plane, b->fields + 2 * b->max_plane};
+        const long long o = b->off[i];
+        const int src = 1 - b->icur[i];
+        cudaError_t err;
+        switch (b->precision) {
+            case PREC_FP32:
+                err = launch_moments<float>((const float *)b->buf[src] + o, rd,
+                                            coef_of<float>(in, b->scale), d[0], d[1], nullptr,
+                                            b->stream);
+                break;
+            case PREC_FP64:
+                err = launch_moments<double>((const double *)b->buf[src] + o, rd,
+                                             coef_of<double>(in, b->scale), d[0], d[1], nullptr,
+                                             b->stream);
+                break;
+            case PREC_FP16:
+                err = launch_moments<__half>((const __half *)b->buf[src] + o, rd,
+                                             coef_of<float>(in, b->scale), d[0], d[1], nullptr,
+                                             b->stream);
+                break;
+            default:
+                err = launch_moments<__nv_bfloat16>((const __nv_bfloat16 *)b->buf[src] + o, rd,
+                                                    coef_of<float>(in, b->scale), d[0], d[1],
+                                                    nullptr, b->stream);
+        }
+        if (err != cudaSuccess) return bcuda(b, err, "batch profile moments");
+        channel_profile<<<PROFILE_POINTS, 128, 0, b->stream>>>(
+            d[0], d[1], in.nx, in.ny, b->e_ref, in.bc.delta_e, q_unit_of(in),
+            out + (size_t)i * 2 * PROFILE_POINTS);
+        BCK(b, cudaGetLastError());
+    }
+    BCK(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_init_profiles(lbm_batch *b, const float *profiles) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (!profiles) return bfail(b, LBM_EINVAL, "profiles is NULL");
+    if (b->precision == PREC_FP16 || b->precision == PREC_BF16)
+        return bfail(b, LBM_EUNSUPPORTED, "profile start needs FP32 or FP64 storage");
+    for (int i = 0; i < b->count; ++i)
+        if (!profile_ok(b->inst[i]))
+            return bfail(b, LBM_EUNSUPPORTED, "instance " + std::to_string(i) +
+                                                  ": profiles need the periodic temperature "
+                                                  "gradient and finite tau_R");
+    BGuard g(b->device);
+    drop_graph(b);
+    b->scale = 1.0;
+    BCK(b, upload_table_any(b));
+    for (int i = 0; i < b->count; ++i) {
+        const lbm_instance &in = b->inst[i];
+        const long long n = (long long)in.nx * in.ny;
+        double *de = b->fields, *dqx = b->fields + b->max_plane, *dqy = b->fields + 2 * b->max_plane;
+        long long blocks = (n + 255) / 256;
+        if (blocks > 4096) blocks = 4096;
+        const float *prof = profiles + (size_t)i * 2 * PROFILE_POINTS;
+        double *emean = b->dsums + 5 * i;      // scratch slot of this instance
+        profile_e_mean<<<1, 128, 0, b->stream>>>(prof, in.ny, emean);
+        BCK(b, cudaGetLastError());
+        channel_fields<<<(unsigned)blocks, 256, 0, b->stream>>>(
+            prof, in.nx, in.ny, b->e_ref, in.bc.delta_e, q_unit_of(in), emean, de, dqx, dqy);
+        BCK(b, cudaGetLastError());
+        const long long o = b->off[i];
+        cudaError_t err;
+        if (b->precision == PREC_FP32)
+            err = launch_init<float>(de, dqx, dqy, in.nx, in.ny, b->e_ref, 1.0,
+                                     coef_of<float>(in, 1.0), (float *)b->buf[1] + o,
+                                     (float *)b->buf[0] + o, b->stream);
+        else
+            err = launch_init<double>(de, dqx, dqy, in.nx, in.ny, b->e_ref, 1.0,
+                                      coef_of<double>(in, 1.0), (double *)b->buf[1] + o,
+                                      (double *)b->buf[0] + o, b->stream);
+        if (err != cudaSuccess) return bcuda(b, err, "batch profile init");
+    }
+    BCK(b, cudaMemsetAsync(b->hist, 0, csize(b->precision) * b->htotal, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->cur = 0;
+    b->initialised = true;
+    b->have_prev = false;
+    std::fill(b->active.begin(), b->active.end(), 1);
+    std::fill(b->icur.begin(), b->icur.end(), 0);
+    std::fill(b->steps.begin(), b->steps.end(), 0);
+    std::fill(b->prev_step.begin(), b->prev_step.end(), 0);
+    std::fill(b->good.begin(), b->good.end(), 0);
+    std::fill(b->last_r.begin(), b->last_r.end(), INFINITY);
+    BCK(b, rebuild_items(b));
+    return LBM_OK;
 }
 
 const char *lbm_batch_last_error(const lbm_batch *b) {

@@ -350,3 +350,43 @@ def test_instability_below_tau_bound_matches_mode_matrix():
             assert (b / a) ** (1 / 200) == pytest.approx(max(rates), rel=1e-4)
         else:
             assert b <= 1e-5
+
+
+# --- warm-start network reference ---------------------------------------------
+def test_mlp_gelu_identities():
+    from oracle import mlp
+    x = np.linspace(-6, 6, 101)
+    g = mlp.gelu(x)
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    np.testing.assert_allclose(mlp.gelu(-x), g - x, atol=1e-15)      # Phi(-x) = 1 - Phi(x)
+    np.testing.assert_allclose(mlp.gelu(np.array([8.0]))[0], 8.0, rtol=1e-14)
+    assert mlp.gelu(np.array([1.0]))[0] == pytest.approx(0.8413447460685429, rel=1e-15)
+    h = 1e-6
+    np.testing.assert_allclose(mlp.gelu_grad(x), (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h),
+                               atol=1e-8)
+
+
+def test_mlp_gradient_against_central_differences():
+    from oracle import mlp
+    widths = [3, 7, 5, 4]
+    rng = np.random.default_rng(4)
+    n = sum(a * b + b for a, b in zip(widths[:-1], widths[1:]))
+    p = rng.normal(0, 0.7, n)
+    x = rng.normal(0, 1, (6, 3))
+    t = rng.normal(0, 1, (6, 4))
+    loss, g = mlp.loss_grad(p, widths, x, t)
+    h = 1e-6
+    num = np.empty(n)
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h
+        num[i] = (mlp.loss_grad(p + e, widths, x, t)[0] - mlp.loss_grad(p - e, widths, x, t)[0]) / (2 * h)
+    np.testing.assert_allclose(g, num, rtol=1e-6, atol=1e-9)
+    # a network with no hidden layer is a least-squares fit: gradient closed form
+    W = rng.normal(size=(2, 3))
+    b = rng.normal(size=2)
+    t2 = rng.normal(size=(6, 2))
+    l2, g2 = mlp.loss_grad(np.concatenate([W.ravel(), b]), [3, 2], x, t2)
+    r = x @ W.T + b - t2
+    np.testing.assert_allclose(g2[:6], (2 * r.T @ x / r.size).ravel(), rtol=1e-13)
+    np.testing.assert_allclose(g2[6:], 2 * r.sum(0) / r.size, rtol=1e-13)
