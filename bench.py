@@ -63,11 +63,18 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="heat_mode", choices=["heat_mode", "batch"],
+    ap.add_argument("--workload", default="heat_mode",
+                    choices=["heat_mode", "batch", "warmstart"],
                     help="heat_mode: 8192^2 throughput (default); batch: 512 channels "
-                         "solved to steady state")
+                         "solved to steady state; warmstart: learned warm start vs cold "
+                         "start on 512 held-out channels")
+    ap.add_argument("--train-instances", type=int, default=4096)
+    ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--check-every", type=int, default=500,
+                    help="steps per residual window (FP32 rounding puts a floor of about "
+                         "1e-6/K under the residual of high-tau channels)")
     ap.add_argument("--max-steps", type=int, default=400000)
     ap.add_argument("--sequential-sample", type=int, default=16)
     return ap.parse_args()
@@ -187,10 +194,18 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+# sources that define each stream-collide kernel
+KERNEL_SOURCES = {
+    "step_vector": ["lbm_device.cuh", "vector_pull.cuh", "stream_collide.cu"],
+    "step_staged": ["lbm_device.cuh", "staged.cu"],
+    "step_scalar": ["lbm_device.cuh", "stream_collide.cu"],
+}
+
+
+def kernel_source_hash(kernel_name):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2010_01847_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES[kernel_name]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -198,11 +213,11 @@ def kernel_source_hash():
 
 def ncu_traffic(kernel_name, precision, nx, ny):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    on the current sources of that kernel (else None), scaled by sites."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel_name not in KERNEL_SOURCES:
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(kernel_name)
     for line in open(path):
         f = line.split()
         if len(f) < 7 or f[0].startswith("#"):
@@ -431,8 +446,8 @@ def batch_instances(n, seed=inputs.SEED):
 
 
 def run_batch(args):
-    """Time to steady state (r < tol on two consecutive checks every 100
-    steps) of the batched channels from a cold start (e = 1, q = 0), with
+    """Time to steady state (r < tol on two consecutive checks every
+    --check-every steps) of the batched channels from a cold start (e = 1, q = 0), with
     the plain single-lattice solver on a sample of them as the baseline."""
     import torch
     import paper_2010_01847_gb300 as plbm
@@ -445,7 +460,7 @@ def run_batch(args):
     b.init()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    steps, r = b.solve(args.tol, 100, args.max_steps)
+    steps, r = b.solve(args.tol, args.check_every, args.max_steps)
     t_batch = time.perf_counter() - t0
     updates = float((steps * sites).sum())
     # plain solver, one lattice at a time, on a seeded sample
@@ -464,8 +479,8 @@ def run_batch(args):
         lat.residual()
         good, n = 0, 0
         while n < args.max_steps:
-            rr, _ = lat.step_residual(100)
-            n += 100
+            rr, _ = lat.step_residual(args.check_every)
+            n += args.check_every
             good = good + 1 if rr < args.tol else 0
             if good >= 2:
                 break
@@ -479,7 +494,8 @@ def run_batch(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batched_channels_{len(inst)}", "instances": len(inst),
                    "rejected_unstable_candidates": rejected,
-                   "total_sites": int(sites.sum()), "tol": args.tol, "check_every": 100,
+                   "total_sites": int(sites.sum()), "tol": args.tol,
+                   "check_every": args.check_every,
                    "schedule": b.schedule, "autotune_us_per_step": tune_us},
         "steps": {"min": int(steps.min()), "median": float(np.median(steps)),
                   "max": int(steps.max()), "all_converged": bool(np.all(r < args.tol))},
@@ -492,12 +508,72 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args):
+    """Learned warm start: steady states of seeded training channels from the
+    batched solver, the network trained on the GPU, then held-out channels
+    (length 4W, a seed the training never saw) solved to r < tol from the
+    cold start and from the predicted profiles."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2010_01847_gb300 import warmstart
+    t0 = time.perf_counter()
+    train = warmstart.channels(args.train_instances, seed=inputs.SEED + 1,
+                               nx=warmstart.TRAIN_NX)
+    prof, tsteps, tr, t_gen = warmstart.steady_profiles(train, args.tol, args.check_every)
+    ws = warmstart.WarmStart(seed=0, max_batch=max(512, args.train_instances))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = ws.train(warmstart.features(train), prof, steps=args.train_steps, batch=512, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    test = warmstart.channels(args.instances, seed=inputs.SEED + 2)
+    t2 = time.perf_counter()
+    pred = ws.predict(test)
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t2
+    cold_steps, cold_r, t_cold, cold = warmstart.solve(test, None, args.tol, args.check_every,
+                                                       args.max_steps)
+    warm_steps, warm_r, t_warm, warm = warmstart.solve(test, pred, args.tol, args.check_every,
+                                                       args.max_steps)
+    sites = np.array([i["nx"] * i["ny"] for i in test], dtype=np.float64)
+    # agreement of the two steady states (relative to each field's range)
+    de, dq = 0.0, 0.0
+    for k in range(len(test)):
+        ce, cq, _ = cold.moments(k)
+        we, wq, _ = warm.moments(k)
+        de = max(de, float(np.abs(we - ce).max() / max(np.abs(ce - ce.mean()).max(), 1e-300)))
+        dq = max(dq, float(np.abs(wq - cq).max() / max(np.abs(cq).max(), 1e-300)))
+    line = {
+        "metric": "time to steady state (r < 1e-8), held-out channels, warm vs cold start",
+        "value": t_warm, "unit": "s", "n_gpus": 1, "higher_is_better": False,
+        "dtype": "f32 solve / bf16 network", "data": "synthetic",
+        "config": {"workload": f"warm_start_{len(test)}_held_out", "tol": args.tol,
+                   "check_every": args.check_every,
+                   "train_instances": len(train), "train_steps": args.train_steps,
+                   "network": list(warmstart.WIDTHS)},
+        "cold_seconds": t_cold, "warm_seconds": t_warm, "speedup": t_cold / t_warm,
+        "cold_steps": {"median": float(np.median(cold_steps)), "max": int(cold_steps.max()),
+                       "site_updates": float((cold_steps * sites).sum())},
+        "warm_steps": {"median": float(np.median(warm_steps)), "max": int(warm_steps.max()),
+                       "site_updates": float((warm_steps * sites).sum())},
+        "all_converged": bool(np.all(cold_r < args.tol) and np.all(warm_r < args.tol)),
+        "steady_state_agreement": {"max_rel_e": de, "max_rel_q": dq},
+        "training": {"data_generation_seconds": t_gen, "data_steps_median": float(np.median(tsteps)),
+                     "train_seconds": t_train, "loss_first": hist[0], "loss_last": hist[-1],
+                     "predict_seconds": t_pred},
+        "total_seconds": time.perf_counter() - t0,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "warmstart":
+        run_warmstart(args)
     else:
         run_native(args)
 

@@ -32,6 +32,9 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 PERIODIC = 0
 PERIODIC_GRADIENT = 1
 WALLS = 2
+SIDES = 3
+# side treatments, sides numbered left, right, bottom, top
+DIFFUSE, ISOTHERMAL, HEAT_FLUX = 0, 1, 2
 
 # Eq. 14 in the order Eqs. 59-60 imply; index i = paper direction i+1.
 CX = np.array([1, 0, -1, 0, 1, -1, -1, 1])
@@ -75,6 +78,11 @@ def _load():
         lib.orc_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, dp, ctypes.c_long]
+        lib.orc_run_sides.restype = ctypes.c_int
+        lib.orc_run_sides.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_int), dp,
+                                      ctypes.c_double, ctypes.c_double, dp, ctypes.c_long]
         lib.orc_moments.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     dp, dp, dp, dp]
         lib.orc_set_threads.argtypes = [ctypes.c_int]
@@ -146,13 +154,18 @@ class Lattice:
 
     def __init__(self, nx: int, ny: int, tau_N: float, tau_R: float,
                  bc_x: int = PERIODIC, bc_y: int = PERIODIC,
-                 delta_e: float = 0.0):
+                 delta_e: float = 0.0, sides=None):
         self.nx, self.ny = int(nx), int(ny)
         self.tau_N, self.tau_R = float(tau_N), float(tau_R)
         self.bc_x, self.bc_y = int(bc_x), int(bc_y)
         self.delta_e = float(delta_e)
         self.f = np.zeros((self.ny, self.nx, 8))
         self.step_count = 0
+        # [(kind, value)] x 4: left, right, bottom, top
+        self.sides = list(sides) if sides is not None else [(DIFFUSE, 0.0)] * 4
+
+    def set_side(self, side: int, kind: int, value: float = 0.0) -> None:
+        self.sides[side] = (int(kind), float(value))
 
     def init(self, e, qx=None, qy=None) -> None:
         shape = (self.ny, self.nx)
@@ -170,9 +183,11 @@ class Lattice:
             self.ny, self.nx, 8).copy()
 
     def step(self, n: int = 1) -> None:
-        rc = _load().orc_run(self.nx, self.ny, self.bc_x, self.bc_y,
-                             self.delta_e, self.tau_N, self.tau_R,
-                             _ptr(self.f), int(n))
+        kinds = (ctypes.c_int * 4)(*[k for k, _ in self.sides])
+        vals = np.array([v for _, v in self.sides], dtype=np.float64)
+        rc = _load().orc_run_sides(self.nx, self.ny, self.bc_x, self.bc_y,
+                                   self.delta_e, kinds, _ptr(vals), self.tau_N,
+                                   self.tau_R, _ptr(self.f), int(n))
         if rc != 0:
             raise ValueError("oracle rejected the lattice parameters")
         self.step_count += int(n)
@@ -188,9 +203,9 @@ class Lattice:
 
 
 def run(nx, ny, tau_N, tau_R, e, qx=None, qy=None, steps=0,
-        bc_x=PERIODIC, bc_y=PERIODIC, delta_e=0.0):
+        bc_x=PERIODIC, bc_y=PERIODIC, delta_e=0.0, sides=None):
     """Convenience: initialise, advance ``steps`` and return the lattice."""
-    lat = Lattice(nx, ny, tau_N, tau_R, bc_x, bc_y, delta_e)
+    lat = Lattice(nx, ny, tau_N, tau_R, bc_x, bc_y, delta_e, sides)
     lat.init(e, qx, qy)
     if steps:
         lat.step(steps)

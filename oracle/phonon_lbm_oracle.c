@@ -16,7 +16,8 @@
  *      temperature-gradient condition (Eqs. 59-60) on the x seam; populations
  *      that leave through a wall are dropped;
  *   3. overwrite the unknown populations of wall nodes by the diffuse
- *      adiabatic reflection (Eq. 58).
+ *      adiabatic reflection (Eq. 58), or, on sides with their own
+ *      treatment, by Eq. 57 (incident heat flux) or Eq. 55 (isothermal).
  * The state "at step n" is the set of populations after stream + boundary of
  * step n, before collision.
  *
@@ -45,8 +46,15 @@
 #include <omp.h>
 #endif
 
-/* Boundary kinds (oracle's own numbering). */
-enum { ORC_PERIODIC = 0, ORC_PERIODIC_GRADIENT = 1, ORC_WALLS = 2 };
+/* Boundary kinds (oracle's own numbering).  ORC_SIDES: the direction is not
+ * periodic and each of its two sides has its own treatment (below). */
+enum { ORC_PERIODIC = 0, ORC_PERIODIC_GRADIENT = 1, ORC_WALLS = 2, ORC_SIDES = 3 };
+
+/* Side treatments (Section 2.5): diffuse adiabatic reflection (Eq. 58),
+ * isothermal equilibrium at e_s = C_V T_s (Eq. 55), incident heat flux q_0
+ * (Eq. 57).  Sides are numbered left (x = 0), right (x = nx-1), bottom
+ * (y = 0), top (y = ny-1). */
+enum { ORC_DIFFUSE = 0, ORC_ISOTHERMAL = 1, ORC_HEAT_FLUX = 2 };
 
 /* Eq. 14: lattice velocities in units of c. */
 static const int CX[8] = {1, 0, -1, 0, 1, -1, -1, 1};
@@ -153,10 +161,69 @@ void orc_init(int nx, int ny, const double *e, const double *qx,
 
 static int wrap(int v, int n) { return ((v % n) + n) % n; }
 
+/* Eq. 57 (Eq. 58 when q0 = 0) at one boundary node with external normal
+ * (nxo, nyo): the populations leaving the surface into the domain
+ * (c . n < 0) are w_i / sum_leaving(w) times the sum of the incident ones
+ * (c . n > 0) plus q0/c (2 tau_r + 1)/(2 tau_r). */
+static void flux_side(double *g, int nxo, int nyo, double q0, double tau_r)
+{
+    double w_leave = 0.0, incident = 0.0;
+    for (int i = 0; i < 8; ++i) {
+        int cn = CX[i] * nxo + CY[i] * nyo;
+        if (cn < 0) w_leave += omega_w(i);
+        if (cn > 0) incident += g[i];
+    }
+    double extra = q0 / flux_factor(tau_r);
+    for (int i = 0; i < 8; ++i)
+        if (CX[i] * nxo + CY[i] * nyo < 0)
+            g[i] = omega_w(i) / w_leave * (incident + extra);
+}
+
+/* Eq. 55: every population of the node at equilibrium at rest at e_s. */
+static void isothermal_node(double *g, double e_s)
+{
+    for (int i = 0; i < 8; ++i) g[i] = omega_w(i) * e_s;
+}
+
+/* Boundary treatment of the sides of ORC_SIDES directions, after
+ * streaming.  A node on an isothermal side is set by Eq. 55 (an x side's
+ * value first when two isothermal sides meet at a corner); otherwise its
+ * y side, then its x side, applies Eq. 57 / Eq. 58 (the paper's cases have
+ * no such corner). */
+static void sides_pass(int nx, int ny, int bc_x, int bc_y, const int *kind,
+                       const double *val, double tau_r, double *f)
+{
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            int on[4] = {0, 0, 0, 0};
+            if (bc_x == ORC_SIDES) { on[0] = x == 0; on[1] = x == nx - 1; }
+            if (bc_y == ORC_SIDES) { on[2] = y == 0; on[3] = y == ny - 1; }
+            if (!(on[0] || on[1] || on[2] || on[3])) continue;
+            double *g = f + ((long)y * nx + x) * 8;
+            int iso = -1;
+            for (int sd = 0; sd < 4 && iso < 0; ++sd)
+                if (on[sd] && kind[sd] == ORC_ISOTHERMAL) iso = sd;
+            if (iso >= 0) {
+                isothermal_node(g, val[iso]);
+                continue;
+            }
+            static const int order[4] = {2, 3, 0, 1};
+            static const int nrm[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+            for (int o = 0; o < 4; ++o) {
+                int sd = order[o];
+                if (!on[sd]) continue;
+                double q0 = kind[sd] == ORC_HEAT_FLUX ? val[sd] : 0.0;
+                flux_side(g, nrm[sd][0], nrm[sd][1], q0, tau_r);
+            }
+        }
+    }
+}
+
 /* One time step in place: collision, push streaming with periodic wrap and
- * the Eq. 59-60 seam jump, then Eq. 58 on wall rows.  tmp holds nx*ny*8
- * doubles of scratch. */
+ * the Eq. 59-60 seam jump, then the boundary treatments.  tmp holds
+ * nx*ny*8 doubles of scratch. */
 static void one_step(int nx, int ny, int bc_x, int bc_y, double delta_e,
+                     const int *kind, const double *val,
                      double tau, double tau_r, double *f, double *tmp)
 {
     long n_sites = (long)nx * ny;
@@ -181,11 +248,13 @@ static void one_step(int nx, int ny, int bc_x, int bc_y, double delta_e,
                 int ty = y + CY[i];
                 double v = src[i];
                 if (ty < 0 || ty >= ny) {
-                    if (bc_y == ORC_WALLS)
+                    if (bc_y == ORC_WALLS || bc_y == ORC_SIDES)
                         continue;           /* leaves through the wall */
                     ty = wrap(ty, ny);
                 }
                 if (tx < 0 || tx >= nx) {
+                    if (bc_x == ORC_SIDES)
+                        continue;           /* leaves through the side */
                     if (bc_x == ORC_PERIODIC_GRADIENT) {
                         /* Eq. 59: i = 1,5,8 entering on the left gain
                          * w_i (e_h - e_c); Eq. 60: i = 3,6,7 entering on
@@ -221,25 +290,41 @@ static void one_step(int nx, int ny, int bc_x, int bc_y, double delta_e,
             }
         }
     }
+
+    /* 4. isothermal / heat-flux / diffuse sides, Eqs. 55, 57, 58 */
+    if (bc_x == ORC_SIDES || bc_y == ORC_SIDES)
+        sides_pass(nx, ny, bc_x, bc_y, kind, val, tau_r, f);
 }
 
 /* Advance n_steps time steps.  bc_x: ORC_PERIODIC or ORC_PERIODIC_GRADIENT;
  * bc_y: ORC_PERIODIC or ORC_WALLS.  delta_e = e_h - e_c of Eqs. 59-60.
  * Returns 0, or -1 when the arguments are outside the scheme. */
-int orc_run(int nx, int ny, int bc_x, int bc_y, double delta_e,
-            double tau_N, double tau_R, double *f, long n_steps)
+int orc_run_sides(int nx, int ny, int bc_x, int bc_y, double delta_e,
+                  const int *side_kind, const double *side_val,
+                  double tau_N, double tau_R, double *f, long n_steps)
 {
     if (nx < 1 || ny < 1 || (bc_y == ORC_WALLS && ny < 2)) return -1;
     if (bc_x == ORC_WALLS || bc_y == ORC_PERIODIC_GRADIENT) return -1;
+    if ((bc_x == ORC_SIDES && nx < 2) || (bc_y == ORC_SIDES && ny < 2)) return -1;
+    static const int diffuse[4] = {0, 0, 0, 0};
+    static const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+    if (!side_kind) side_kind = diffuse;
+    if (!side_val) side_val = zero;
     double p[3];
     orc_params(tau_N, tau_R, p);
     if (!(p[0] > 0.5)) return -1;
     double *tmp = (double *)malloc(sizeof(double) * 8 * (size_t)nx * ny);
     if (!tmp) return -1;
     for (long n = 0; n < n_steps; ++n)
-        one_step(nx, ny, bc_x, bc_y, delta_e, p[0], p[1], f, tmp);
+        one_step(nx, ny, bc_x, bc_y, delta_e, side_kind, side_val, p[0], p[1], f, tmp);
     free(tmp);
     return 0;
+}
+
+int orc_run(int nx, int ny, int bc_x, int bc_y, double delta_e,
+            double tau_N, double tau_R, double *f, long n_steps)
+{
+    return orc_run_sides(nx, ny, bc_x, bc_y, delta_e, 0, 0, tau_N, tau_R, f, n_steps);
 }
 
 /* e, q of every node of a state (Eqs. 53-54). */

@@ -51,13 +51,17 @@ def mode_matrix(kx: float, ky: float, tau: float, tau_r: float) -> np.ndarray:
 
 
 def step_matrix(nx: int, ny: int, tau: float, tau_r: float, bc_x: int,
-                bc_y: int, delta_e: float) -> np.ndarray:
+                bc_y: int, delta_e: float, sides=None) -> np.ndarray:
     """Dense affine matrix T of size (8N+1)^2 acting on [f; 1], with
     f flattened as f[(y*nx + x)*8 + i] (the oracle's layout).
 
     bc codes: 0 periodic, 1 periodic temperature gradient (x only),
-    2 diffuse adiabatic walls (y only).
+    2 diffuse adiabatic walls (y only), 3 per-side treatments ``sides`` =
+    [(kind, value)] for left, right, bottom, top with kind 0 diffuse
+    (Eq. 58), 1 isothermal at e_s = value (Eq. 55), 2 incident heat flux
+    q_0 = value (Eq. 57).
     """
+    sides = sides or [(0, 0.0)] * 4
     n = nx * ny
     dim = 8 * n + 1
     M = collision_matrix(tau, tau_r)
@@ -74,11 +78,13 @@ def step_matrix(nx: int, ny: int, tau: float, tau_r: float, bc_x: int,
             for i in range(8):
                 ty, tx = y + CY[i], x + CX[i]
                 if not 0 <= ty < ny:
-                    if bc_y == 2:
+                    if bc_y in (2, 3):
                         continue
                     ty %= ny
                 jump = 0.0
                 if not 0 <= tx < nx:
+                    if bc_x == 3:
+                        continue
                     if bc_x == 1:
                         jump = OMEGA[i] * delta_e * (1 if tx >= nx else -1)
                     tx %= nx
@@ -99,4 +105,40 @@ def step_matrix(nx: int, ny: int, tau: float, tau_r: float, bc_x: int,
                     B[base + i, :] = 0.0
                     for j in incident:
                         B[base + i, base + j] = OMEGA[i] / w_leave
-    return B @ P @ C
+    T = B @ P @ C
+    if bc_x == 3 or bc_y == 3:
+        kap = 1.0 if math.isinf(tau_r) else 2 * tau_r / (2 * tau_r + 1)
+        normals = [(-1, 0), (1, 0), (0, -1), (0, 1)]
+        for y in range(ny):
+            for x in range(nx):
+                on = [bc_x == 3 and x == 0, bc_x == 3 and x == nx - 1,
+                      bc_y == 3 and y == 0, bc_y == 3 and y == ny - 1]
+                if not any(on):
+                    continue
+                base = 8 * (y * nx + x)
+                iso = [sd for sd in range(4) if on[sd] and sides[sd][0] == 1]
+                S = np.eye(dim)
+                if iso:
+                    # Eq. 55: node at equilibrium at rest at e_s
+                    for i in range(8):
+                        S[base + i, :] = 0.0
+                        S[base + i, -1] = OMEGA[i] * sides[iso[0]][1]
+                    T = S @ T
+                    continue
+                for sd in (2, 3, 0, 1):
+                    if not on[sd]:
+                        continue
+                    nxo, nyo = normals[sd]
+                    cn = CX * nxo + CY * nyo
+                    inc = [i for i in range(8) if cn[i] > 0]
+                    lev = [i for i in range(8) if cn[i] < 0]
+                    wl = OMEGA[lev].sum()
+                    q0 = sides[sd][1] if sides[sd][0] == 2 else 0.0
+                    S = np.eye(dim)
+                    for i in lev:
+                        S[base + i, :] = 0.0
+                        for j in inc:
+                            S[base + i, base + j] = OMEGA[i] / wl
+                        S[base + i, -1] = OMEGA[i] / wl * q0 / kap
+                    T = S @ T
+    return T

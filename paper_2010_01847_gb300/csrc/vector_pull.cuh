@@ -156,59 +156,57 @@ __device__ __forceinline__ VecPos vector_pull(const T *__restrict__ src, int nx,
     const bool bottom = walls && y == 0;
     const bool top = walls && y == ny - 1;
 
-    long long row_off[8];
+    // every load is issued before any is used: the 16-byte vectors and, for
+    // the lanes at a warp edge or a row end, the one neighbouring element of
+    // each x-shifted plane (so a warp waits for one memory round trip)
+    const bool need_left = (lane == 0 || xv == 0) && active;
+    const bool need_right = (lane == 31 || xv + 1 == tpr) && active;
+    const int sx_left = x0 == 0 ? nx - 1 : x0 - 1;
+    const int sx_right = x0 + V >= nx ? x0 + V - nx : x0 + V;
+    C edge[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const int cy = cy_of(i);
+        const int cx = cx_of(i), cy = cy_of(i);
         int sy = y - cy;
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-        row_off[i] = (long long)i * plane + (long long)sy * nx;
+        const long long row = (long long)i * plane + (long long)sy * nx;
         const bool unknown = (cy > 0 && bottom) || (cy < 0 && top);
         if (active && !unknown) {
-            Pack<T>::unpack(ld_stream(src + row_off[i] + x0), d[i]);
+            Pack<T>::unpack(ld_stream(src + row + x0), d[i]);
         } else {
 #pragma unroll
             for (int j = 0; j < V; ++j) d[i][j] = C(0);
         }
+        edge[i] = C(0);
+        if (cx > 0 && need_left && !unknown) edge[i] = Store<T>::load(src[row + sx_left]);
+        if (cx < 0 && need_right && !unknown) edge[i] = Store<T>::load(src[row + sx_right]);
     }
 
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i);
+        const int cx = cx_of(i);
         if (cx == 0) continue;
-        const bool unknown = (cy > 0 && bottom) || (cy < 0 && top);
         const C jw = (i < 4) ? k.jump_axis : k.jump_diag;
         if (cx > 0) {
             C left = __shfl_up_sync(0xffffffffu, d[i][V - 1], 1);
-            if ((lane == 0 || xv == 0) && active && !unknown) {
-                int sx = x0 - 1;
-                C jump = C(0);
-                if (sx < 0) {
-                    sx += nx;
-                    if (bc_x == BC_GRADIENT) jump = jw;
-                }
-                left = Store<T>::load(src[row_off[i] + sx]) + jump;
+            if (need_left) {
+                // crossing the seam moving right (Eq. 59)
+                left = edge[i] + ((x0 == 0 && bc_x == BC_GRADIENT) ? jw : C(0));
             }
 #pragma unroll
             for (int j = V - 1; j >= 1; --j) d[i][j] = d[i][j - 1];
             d[i][0] = left;
         } else {
             C right = __shfl_down_sync(0xffffffffu, d[i][0], 1);
-            if ((lane == 31 || xv + 1 == tpr) && active && !unknown) {
-                int sx = x0 + V;
-                C jump = C(0);
-                if (sx >= nx) {
-                    sx -= nx;
-                    if (bc_x == BC_GRADIENT) jump = -jw;
-                }
-                right = Store<T>::load(src[row_off[i] + sx]) + jump;
+            if (need_right) {
+                // crossing the seam moving left (Eq. 60)
+                right = edge[i] - ((x0 + V == nx && bc_x == BC_GRADIENT) ? jw : C(0));
             }
 #pragma unroll
             for (int j = 0; j < V - 1; ++j) d[i][j] = d[i][j + 1];
             d[i][V - 1] = right;
         }
     }
-
     return VecPos{y, xv, x0, active, bottom, top};
 }
 
