@@ -64,10 +64,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="heat_mode",
-                    choices=["heat_mode", "batch", "warmstart"],
+                    choices=["heat_mode", "batch", "warmstart", "d3q14"],
                     help="heat_mode: 8192^2 throughput (default); batch: 512 channels "
                          "solved to steady state; warmstart: learned warm start vs cold "
-                         "start on 512 held-out channels")
+                         "start on 512 held-out channels; d3q14: 3-D D3Q14 throughput "
+                         "on a periodic nz x ny x nx lattice (--n3 cells per side)")
+    ap.add_argument("--n3", type=int, default=512)
     ap.add_argument("--train-instances", type=int, default=4096)
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--instances", type=int, default=512)
@@ -423,6 +425,62 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_d3q14(args):
+    """Throughput of the D3Q14 stream-collide step (lbm_nd_*): periodic n^3
+    lattice, x-directed sine mode of wavelength 512 cells (+ U[-1e-6, 1e-6)
+    noise), Kn as the 2-D heat-mode workload, FP32 or FP64 storage."""
+    import torch
+    import paper_2010_01847_gb300 as plbm
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = args.n3
+    w = inputs.THROUGHPUT_8192
+    speed = plbm.LatticeND.lattice_speed(plbm.D3Q14)
+    tau_N, tau_R = w.kn_N * w.length * speed, w.kn_R * w.length * speed
+    x = np.arange(n, dtype=np.float64)
+    e = np.empty((n, n, n))
+    e[...] = 1.0 + 1e-3 * np.sin(2 * np.pi * x / 512.0)
+    e += inputs.uniform_noise(e.shape, 1e-6)
+    prec = args.precision if args.precision in ("fp32", "fp64") else "fp32"
+    lat = plbm.LatticeND(plbm.D3Q14, (n, n, n), tau_N, tau_R, precision=prec)
+    lat.init(e)
+    e0 = lat.energy()
+    stream = torch.cuda.current_stream(dev)
+    lat.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index)
+    with sampler:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        lat.step(args.steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    sites = n ** 3
+    bps = 2 * 14 * STORAGE_BYTES[prec]
+    achieved = bps * sites * args.steps / elapsed / 1e9
+    peak, peak_kind = measured_peak()
+    drift = abs(lat.energy() - e0) / abs(e0)
+    line = {
+        "metric": "GLUPS & % HBM roofline (D3Q14)", "value": sites * args.steps / elapsed / 1e9,
+        "unit": "GLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+        "config": {"workload": f"d3q14_heat_mode_{n}^3", "lattice": "D3Q14",
+                   "kn_N": w.kn_N, "kn_R": w.kn_R, "length_cells": w.length,
+                   "storage": f"{prec} deviation",
+                   "l2": "inputs larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_kind, "kernel": "step_nd",
+                     "bytes_per_site_update": bps},
+        "clocks": sampler.summary(), "gpu_launches": args.steps, "e2e": None,
+        "cpu_baseline": None, "energy_drift": drift,
+    }
+    print(json.dumps(line), flush=True)
+    lat.close()
+
+
 def batch_instances(n, seed=inputs.SEED):
     """The batched-channel workload: seeded candidates (width W in [16, 512],
     length 4W, Kn_N log-U[1e-3, 1e-1], Kn_R log-U[0.1, 10], walls, periodic
@@ -574,6 +632,8 @@ def main():
         run_batch(args)
     elif args.workload == "warmstart":
         run_warmstart(args)
+    elif args.workload == "d3q14":
+        run_d3q14(args)
     else:
         run_native(args)
 

@@ -20,8 +20,11 @@
  * x = nx-1 to x = 0 gain w_i delta_e, those crossing back lose it); diffuse
  * adiabatic walls on the rows y = 0 and y = ny-1 (Eq. 58: the unknown
  * populations of a wall node are w_i / (5/18) times the sum of its incident
- * ones).  Walls sit on the boundary nodes; they act right after streaming;
- * wall nodes then collide like every other node.
+ * ones); and non-periodic directions whose two sides each carry their own
+ * treatment (lbm_set_side): diffuse adiabatic (Eq. 58), isothermal (Eq. 55)
+ * or an incident heat flux (Eqs. 56-57).  Boundaries sit on the boundary
+ * nodes; they act right after streaming; boundary nodes then collide like
+ * every other node.
  *
  * STATE CONTRACT.  "The state at step n" is the set of populations after
  * streaming and boundary treatment of step n, before collision.  lbm_init
@@ -64,8 +67,43 @@ typedef enum {
 typedef enum {
     LBM_BC_PERIODIC = 0,            /* plain wrap                              */
     LBM_BC_PERIODIC_GRADIENT = 1,   /* Eqs. 59-60; x direction only            */
-    LBM_BC_DIFFUSE_WALLS = 2        /* Eq. 58 on rows 0 and ny-1; y only       */
+    LBM_BC_DIFFUSE_WALLS = 2,       /* Eq. 58 on rows 0 and ny-1; y only       */
+    LBM_BC_SIDES = 3                /* not periodic: each of the two sides has */
+                                    /* its own treatment (lbm_set_side), by    */
+                                    /* default diffuse adiabatic; x or y       */
 } lbm_bc;
+
+/* The four sides of the lattice (external normals (-1,0), (1,0), (0,-1),
+ * (0,1)): the nodes x = 0, x = nx-1, y = 0 and y = ny-1. */
+typedef enum {
+    LBM_SIDE_LEFT = 0,
+    LBM_SIDE_RIGHT = 1,
+    LBM_SIDE_BOTTOM = 2,
+    LBM_SIDE_TOP = 3
+} lbm_side;
+
+/* Treatments of a side of an LBM_BC_SIDES direction (Section 2.5).  With
+ * n the side's external normal and kappa = 2 tau_r / (2 tau_r + 1):
+ *   LBM_SIDE_DIFFUSE     Eq. 58: the unknown populations (c_i . n < 0) are
+ *                        w_i / (5/18) times the sum of the incident ones
+ *                        (c_i . n > 0); no energy crosses the side.
+ *   LBM_SIDE_ISOTHERMAL  Eq. 55: every population of the node is set to
+ *                        w_i e_s, the equilibrium at rest at the side's
+ *                        energy density e_s (= C_V T_s).
+ *   LBM_SIDE_HEAT_FLUX   Eq. 57: the unknown populations are w_i / (5/18)
+ *                        times (sum of the incident ones + q_0 / kappa), so
+ *                        that -kappa sum_i (c_i . n) e_i = q_0 (Eq. 56): q_0
+ *                        is the flux entering the lattice through the side.
+ * A node on two sides (a corner) takes the isothermal treatment of the
+ * first isothermal side in the order left, right, bottom, top.  A corner
+ * between a LBM_BC_SIDES x side and a y side (walls or a side) with no
+ * isothermal side among them has no treatment in the scheme: calls that
+ * advance or read such a lattice return LBM_EUNSUPPORTED. */
+typedef enum {
+    LBM_SIDE_DIFFUSE = 0,
+    LBM_SIDE_ISOTHERMAL = 1,
+    LBM_SIDE_HEAT_FLUX = 2
+} lbm_side_kind;
 
 /* How the populations are stored in device memory.  All but LBM_FP64 store
  * the deviation d_i = s (e_i - w_i e_ref) from the equilibrium at rest at the
@@ -83,7 +121,8 @@ typedef enum {
 /* Which stream-collide kernel lbm_step launches. */
 typedef enum {
     LBM_KERNEL_AUTO = 0,     /* fastest kernel valid for the lattice          */
-    LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx                   */
+    LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx; the only kernel  */
+                             /* for lattices with LBM_BC_SIDES                */
     LBM_KERNEL_VECTOR = 2,   /* 16-byte vectors along x; nx % (16/size) == 0  */
     LBM_KERNEL_STAGED = 3    /* bulk asynchronous copies (TMA engine) of row  */
                              /* segments into a shared-memory ring; needs nx  */
@@ -97,8 +136,8 @@ typedef struct {
 } lbm_grid;
 
 typedef struct {
-    int x;                   /* LBM_BC_PERIODIC or LBM_BC_PERIODIC_GRADIENT    */
-    int y;                   /* LBM_BC_PERIODIC or LBM_BC_DIFFUSE_WALLS        */
+    int x;                   /* LBM_BC_PERIODIC, _PERIODIC_GRADIENT or _SIDES  */
+    int y;                   /* LBM_BC_PERIODIC, _DIFFUSE_WALLS or _SIDES      */
     double delta_e;          /* e_h - e_c of Eqs. 59-60 across one x period    */
 } lbm_boundary;
 
@@ -116,6 +155,7 @@ size_t lbm_population_bytes(lbm_grid grid, lbm_precision precision);
  * rounding).  stream is a cudaStream_t (NULL = legacy default stream) on the
  * current device, which the context remembers.
  * Allocates two population buffers with cudaMalloc; freed by lbm_destroy.
+ * The sides of LBM_BC_SIDES directions start diffuse (Eq. 58).
  * Errors: EINVAL (NULL out, grid too small, tau <= 1/2, tau_R <= 0, bad
  * enum), EUNSUPPORTED (gradient on y, walls on x), ENOMEM, ECUDA. */
 lbm_status lbm_create(lbm_grid grid, double tau_N, double tau_R,
@@ -206,6 +246,24 @@ lbm_status lbm_set_kernel(lbm_ctx *ctx, int kernel);
 
 /* The kernel lbm_step will launch (never LBM_KERNEL_AUTO). */
 int lbm_get_kernel(const lbm_ctx *ctx);
+
+/* Set the treatment of one side of an LBM_BC_SIDES direction (Section 2.5;
+ * see lbm_side_kind).  side: LBM_SIDE_*; kind: LBM_SIDE_*; value: e_s (the
+ * side's energy density, same units as e) for ISOTHERMAL, q_0 (the heat
+ * flux entering through the side, lattice units) for HEAT_FLUX, ignored for
+ * DIFFUSE.  Takes effect from the next step; the state is kept, so a
+ * treatment can be switched between steps (the heat pulse of Section 3.4:
+ * HEAT_FLUX for the pulse, then DIFFUSE).  Side values do not enter the
+ * checkpoint of lbm_get_state.  With 16-bit storage, set the sides before
+ * lbm_init, which sizes the storage scale for them too.
+ * Errors: EINVAL (NULL ctx, bad side or kind, the side's direction is not
+ * LBM_BC_SIDES, non-finite value, or a value too large for the 16-bit
+ * scale already fixed by lbm_init). */
+lbm_status lbm_set_side(lbm_ctx *ctx, int side, int kind, double value);
+
+/* The treatment and value of a side (kind and value may be NULL).
+ * Errors: EINVAL (NULL ctx, bad side). */
+lbm_status lbm_get_side(const lbm_ctx *ctx, int side, int *kind, double *value);
 
 /* Launch shape of the staged kernel; results do not depend on it.
  *   stages          shared-memory ring depth, 2..6 (0 = default 2)
@@ -410,6 +468,74 @@ lbm_status lbm_residual_noalloc(const double *e, const double *qx, const double 
                                 const double *prev_e, const double *prev_qx,
                                 const double *prev_qy, long long n_nodes, double e_ref,
                                 long k_steps, void *stream, double *r, double *total_energy);
+
+/* ------------------------------------------------------------------------ *
+ * The D1Q2 and D3Q14 lattices (periodic lattices only).
+ *
+ * Section 2.2 says the scheme extends to the one-dimensional D1Q2 and the
+ * three-dimensional D3Q14 lattices without giving their weights.  These
+ * calls use the weights the Chapman-Enskog analysis of Section 2.3 requires
+ * of a velocity set: sum w_i = 1, sum w_i c_ia c_ib = (5/9) delta_ab, sum
+ * h_i c_ia c_ib = delta_ab and an isotropic fourth moment sum h_i c c c c =
+ * (1/3)(dd + dd + dd), with e_i^eq = w_i e + h_i c_i . q (Eq. 15) and
+ * S_i = -(1 - 1/(2 tau)) h_i c_i . q / tau_r (Eq. 16):
+ *   D3Q14: c_i = (+-1,0,0), (0,+-1,0), (0,0,+-1) with w = 1/9, h = 1/3;
+ *          (+-1,+-1,+-1) with w = 1/24, h = 1/24.  It recovers Eqs. 6-7 in
+ *          three dimensions with the lattice speed c = sqrt(3/5) v_g of
+ *          Eq. 48 and tau = tau_C + 1/2 (Eq. 49).
+ *   D1Q2:  c_i = +-1, w = h = 1/2.  Two velocities cannot carry the nonlocal
+ *          term of Eq. 7: the lattice recovers Eq. 6 and Eq. 7 without it
+ *          (the Cattaneo equation), with c = v_g / sqrt(3).
+ * Directions (population plane order): D3Q14 +x, -x, +y, -y, +z, -z, then
+ * +b, -b for b = (1,1,1), (1,1,-1), (1,-1,1), (1,-1,-1); D1Q2 +x, -x.
+ * Layout: host arrays [nz][ny][nx] float64 (index (z*ny + y)*nx + x); a
+ * flux array holds dim planes (x, then y, then z).  Populations are stored
+ * as FP32 or FP64 deviations from w_i e_ref; the state contract, the graph
+ * chunks and the error conventions are those of the D2Q8 calls above. */
+typedef enum {
+    LBM_LATTICE_D1Q2 = 1,
+    LBM_LATTICE_D3Q14 = 3
+} lbm_lattice;
+
+typedef struct lbm_nd lbm_nd;
+
+/* c / v_g of a lattice (sqrt(3/5) for D3Q14, 1/sqrt(3) for D1Q2; 0 for an
+ * unknown lattice): a Knudsen number Kn over L cells gives the relaxation
+ * time Kn * L * (c / v_g) in steps. */
+double lbm_nd_lattice_speed(int lattice);
+
+/* Create a periodic nx x ny x nz lattice (D1Q2: ny = nz = 1).  tau_N, tau_R
+ * as for lbm_create; precision LBM_FP32 or LBM_FP64.  Allocates two
+ * population buffers of Q * nx * ny * nz elements.
+ * Errors: EINVAL (bad lattice, sizes, tau, e_ref, NULL out), EUNSUPPORTED
+ * (16-bit storage), ENOMEM, ECUDA (text from lbm_nd_last_error(NULL)). */
+lbm_status lbm_nd_create(int lattice, int nx, int ny, int nz, double tau_N, double tau_R,
+                         int precision, double e_ref, void *stream, lbm_nd **out);
+
+/* Step 0 = Eq. 15 from HOST e[n] and q[dim][n] (q may be NULL for zero).
+ * Synchronises.  Errors: EINVAL (NULL, non-finite input), ECUDA. */
+lbm_status lbm_nd_init(lbm_nd *ctx, const double *e, const double *q);
+
+/* Advance n >= 0 steps (async; 64-step CUDA graphs for long runs). */
+lbm_status lbm_nd_step(lbm_nd *ctx, long n);
+
+/* Wait for the queued work. */
+lbm_status lbm_nd_sync(lbm_nd *ctx);
+
+/* e[n] and q[dim][n] (HOST, either may be NULL) of the current state
+ * (Eqs. 53-54).  Synchronises. */
+lbm_status lbm_nd_moments(lbm_nd *ctx, double *e, double *q);
+
+/* Populations e_i of the current state, HOST f[Q][n].  Synchronises. */
+lbm_status lbm_nd_populations(lbm_nd *ctx, double *f);
+
+/* Total energy sum e of the current state (FP64 reduction, deterministic).
+ * ENONFINITE if the state holds NaN or Inf.  Synchronises. */
+lbm_status lbm_nd_energy(lbm_nd *ctx, double *total);
+
+long lbm_nd_step_count(const lbm_nd *ctx);
+void lbm_nd_destroy(lbm_nd *ctx);
+const char *lbm_nd_last_error(const lbm_nd *ctx);
 
 #ifdef __cplusplus
 }

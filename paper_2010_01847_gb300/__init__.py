@@ -21,10 +21,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libphonon_lbm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(7)
-PERIODIC, PERIODIC_GRADIENT, DIFFUSE_WALLS = 0, 1, 2
+PERIODIC, PERIODIC_GRADIENT, DIFFUSE_WALLS, SIDES = 0, 1, 2, 3
+LEFT, RIGHT, BOTTOM, TOP = 0, 1, 2, 3                 # sides (lbm_side)
+DIFFUSE, ISOTHERMAL, HEAT_FLUX = 0, 1, 2              # side treatments (lbm_side_kind)
 FP32, FP16_DEV, BF16_DEV, FP64 = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_STAGED = 0, 1, 2, 3
 
+D1Q2, D3Q14 = 1, 3                                     # lbm_lattice
 PRECISIONS = {"fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV, "fp64": FP64}
 KERNELS = {"auto": KERNEL_AUTO, "scalar": KERNEL_SCALAR, "vector": KERNEL_VECTOR,
            "staged": KERNEL_STAGED}
@@ -37,7 +40,8 @@ EXPORTS = [
     "lbm_moments", "lbm_moments_device", "lbm_populations", "lbm_residual",
     "lbm_step_residual",
     "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_step_count",
-    "lbm_set_kernel", "lbm_get_kernel", "lbm_set_staged_config", "lbm_get_staged_config",
+    "lbm_set_kernel", "lbm_get_kernel", "lbm_set_side", "lbm_get_side",
+    "lbm_set_staged_config", "lbm_get_staged_config",
     "lbm_set_graph_chunk", "lbm_autotune",
     "lbm_kernel_launches", "lbm_storage_scale", "lbm_last_error",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_init", "lbm_batch_step",
@@ -48,6 +52,9 @@ EXPORTS = [
     "lbm_mlp_get_params", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train_step",
     "lbm_mlp_last_error",
     "lbm_residual_noalloc",
+    "lbm_nd_lattice_speed", "lbm_nd_create", "lbm_nd_init", "lbm_nd_step", "lbm_nd_sync",
+    "lbm_nd_moments", "lbm_nd_populations", "lbm_nd_energy", "lbm_nd_step_count",
+    "lbm_nd_destroy", "lbm_nd_last_error",
 ]
 NOALLOC_MAX_NODES = 16777216
 
@@ -110,6 +117,8 @@ def load_library(path: str = LIB_PATH):
         "lbm_step_count": (c_long, [vp]),
         "lbm_set_kernel": (st, [vp, ctypes.c_int]),
         "lbm_get_kernel": (ctypes.c_int, [vp]),
+        "lbm_set_side": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
+        "lbm_get_side": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
         "lbm_set_graph_chunk": (st, [vp, ctypes.c_int]),
         "lbm_autotune": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
         "lbm_set_staged_config": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -147,6 +156,19 @@ def load_library(path: str = LIB_PATH):
         "lbm_mlp_last_error": (ctypes.c_char_p, [vp]),
         "lbm_residual_noalloc": (st, [vp, vp, vp, vp, vp, vp, ctypes.c_longlong,
                                       ctypes.c_double, c_long, vp, dp, dp]),
+        "lbm_nd_lattice_speed": (ctypes.c_double, [ctypes.c_int]),
+        "lbm_nd_create": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                               vp, ctypes.POINTER(vp)]),
+        "lbm_nd_init": (st, [vp, dp, dp]),
+        "lbm_nd_step": (st, [vp, c_long]),
+        "lbm_nd_sync": (st, [vp]),
+        "lbm_nd_moments": (st, [vp, dp, dp]),
+        "lbm_nd_populations": (st, [vp, dp]),
+        "lbm_nd_energy": (st, [vp, dp]),
+        "lbm_nd_step_count": (c_long, [vp]),
+        "lbm_nd_destroy": (None, [vp]),
+        "lbm_nd_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -191,14 +213,17 @@ class Lattice:
 
     Parameters are in lattice units: ``tau_N``, ``tau_R`` are relaxation
     times in steps (``math.inf`` allowed for one of them); ``bc_x`` is
-    PERIODIC or PERIODIC_GRADIENT (with ``delta_e`` = e_h - e_c of
-    Eqs. 59-60), ``bc_y`` is PERIODIC or DIFFUSE_WALLS (Eq. 58).
+    PERIODIC, PERIODIC_GRADIENT (with ``delta_e`` = e_h - e_c of
+    Eqs. 59-60) or SIDES, ``bc_y`` is PERIODIC, DIFFUSE_WALLS (Eq. 58) or
+    SIDES.  The sides of a SIDES direction are set by ``sides`` (a list of
+    four (kind, value) pairs for LEFT, RIGHT, BOTTOM, TOP, or a dict
+    {side: (kind, value)}) or by ``set_side``; see lbm_set_side.
     ``precision`` is one of "fp32", "fp16", "bf16", "fp64".
     """
 
     def __init__(self, nx, ny, tau_N, tau_R, bc_x=PERIODIC, bc_y=PERIODIC, delta_e=0.0,
                  precision="fp32", e_ref=1.0, kernel="auto", device=None,
-                 torch_buffers=True, graph_chunk=None):
+                 torch_buffers=True, graph_chunk=None, sides=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the phonon LBM runs only on the GPU")
@@ -232,6 +257,11 @@ class Lattice:
         if st != OK:
             self._ctx = ctypes.c_void_p()
             raise LBMError(st, self._lib.lbm_last_error(None).decode())
+        if sides is not None:
+            items = sides.items() if isinstance(sides, dict) else enumerate(sides)
+            for side, (kind, value) in items:
+                if kind is not None:
+                    self.set_side(side, kind, value)
         if kernel != "auto":
             self.set_kernel(kernel)
         if graph_chunk is not None:
@@ -290,6 +320,19 @@ class Lattice:
 
     def step(self, n: int = 1):
         self._check(self._lib.lbm_step(self._ctx, int(n)))
+
+    def set_side(self, side: int, kind: int, value: float = 0.0):
+        """Treatment of one side of a SIDES direction (lbm_set_side):
+        DIFFUSE (Eq. 58), ISOTHERMAL at e_s = value (Eq. 55) or HEAT_FLUX
+        with incident flux q_0 = value (Eq. 57)."""
+        self._check(self._lib.lbm_set_side(self._ctx, int(side), int(kind), float(value)))
+
+    def side(self, side: int):
+        """(kind, value) of one side."""
+        k, v = ctypes.c_int(), ctypes.c_double()
+        self._check(self._lib.lbm_get_side(self._ctx, int(side), ctypes.byref(k),
+                                           ctypes.byref(v)))
+        return k.value, v.value
 
     def sync(self):
         self._check(self._lib.lbm_sync(self._ctx))
@@ -601,3 +644,89 @@ class Mlp:
                                                  ctypes.c_void_p(t.data_ptr()), x.shape[0],
                                                  ctypes.c_float(lr), ctypes.byref(loss)))
         return loss.value
+
+
+class LatticeND:
+    """A periodic D1Q2 or D3Q14 lattice on one GPU (lbm_nd_*).
+
+    ``shape`` is (nz, ny, nx) for D3Q14 and (nx,) for D1Q2; fields are numpy
+    float64 arrays of that shape, fluxes carry a leading axis of the
+    lattice's dimension (x, y, z).  ``precision`` is "fp32" or "fp64".
+    """
+
+    def __init__(self, lattice, shape, tau_N, tau_R, precision="fp32", e_ref=1.0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the phonon LBM runs only on the GPU")
+        self._lib = load_library()
+        self.lattice = int(lattice)
+        self.shape = tuple(int(v) for v in shape)
+        self.dim = 3 if self.lattice == D3Q14 else 1
+        if len(self.shape) != self.dim:
+            raise ValueError("shape must have one entry per lattice dimension")
+        nz, ny, nx = (self.shape if self.dim == 3 else (1, 1, self.shape[0]))
+        self.Q = 14 if self.lattice == D3Q14 else 2
+        self.n = nx * ny * nz
+        self.stream = torch.cuda.current_stream()
+        self._ctx = ctypes.c_void_p()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        st = self._lib.lbm_nd_create(self.lattice, nx, ny, nz, float(tau_N), float(tau_R), prec,
+                                     float(e_ref), ctypes.c_void_p(self.stream.cuda_stream),
+                                     ctypes.byref(self._ctx))
+        if st != OK:
+            self._ctx = ctypes.c_void_p()
+            raise LBMError(st, self._lib.lbm_nd_last_error(None).decode())
+
+    def _check(self, st):
+        if st != OK:
+            raise LBMError(st, self._lib.lbm_nd_last_error(self._ctx).decode())
+
+    def close(self):
+        if self._ctx:
+            self._lib.lbm_nd_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def lattice_speed(lattice) -> float:
+        """c / v_g of the lattice (lbm_nd_lattice_speed)."""
+        return load_library().lbm_nd_lattice_speed(int(lattice))
+
+    def init(self, e, q=None):
+        e = np.ascontiguousarray(np.broadcast_to(np.asarray(e, dtype=np.float64), self.shape))
+        qa = None if q is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(q, dtype=np.float64), (self.dim,) + self.shape))
+        self._check(self._lib.lbm_nd_init(self._ctx, _dptr(e),
+                                          _dptr(qa) if qa is not None else None))
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_nd_step(self._ctx, int(n)))
+
+    def sync(self):
+        self._check(self._lib.lbm_nd_sync(self._ctx))
+
+    def moments(self):
+        """(e [shape], q [dim, *shape]) of the current state."""
+        e = np.empty(self.shape)
+        q = np.empty((self.dim,) + self.shape)
+        self._check(self._lib.lbm_nd_moments(self._ctx, _dptr(e), _dptr(q)))
+        return e, q
+
+    def populations(self):
+        f = np.empty((self.Q,) + self.shape)
+        self._check(self._lib.lbm_nd_populations(self._ctx, _dptr(f)))
+        return f
+
+    def energy(self) -> float:
+        v = ctypes.c_double()
+        self._check(self._lib.lbm_nd_energy(self._ctx, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def step_count(self) -> int:
+        return self._lib.lbm_nd_step_count(self._ctx)

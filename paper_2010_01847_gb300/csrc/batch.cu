@@ -323,7 +323,7 @@ Params params_of(const lbm_instance &in) {
 template <typename C>
 Coef<C> coef_of(const lbm_instance &in, double scale) {
     const Params p = params_of(in);
-    Coef<C> k;
+    Coef<C> k{};
     k.omega = (C)(1.0 / p.tau);
     k.sigma = (C)p.sigma;
     k.lambda = (C)p.lambda;
@@ -496,7 +496,8 @@ lbm_status lbm_batch_create(const lbm_instance *inst, int count, lbm_precision p
         if ((in.bc.x != LBM_BC_PERIODIC && in.bc.x != LBM_BC_PERIODIC_GRADIENT) ||
             (in.bc.y != LBM_BC_PERIODIC && in.bc.y != LBM_BC_DIFFUSE_WALLS))
             return bfail(nullptr, in.bc.x == LBM_BC_DIFFUSE_WALLS ||
-                                          in.bc.y == LBM_BC_PERIODIC_GRADIENT
+                                          in.bc.y == LBM_BC_PERIODIC_GRADIENT ||
+                                          in.bc.x == LBM_BC_SIDES || in.bc.y == LBM_BC_SIDES
                                       ? LBM_EUNSUPPORTED
                                       : LBM_EINVAL,
                          at + "unsupported boundary kinds");

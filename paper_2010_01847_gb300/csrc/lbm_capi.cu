@@ -19,6 +19,9 @@ struct lbm_ctx {
     long long plane = 0;
     int bc_x = 0, bc_y = 0;
     double delta_e = 0.0;
+    // sides of LBM_BC_SIDES directions: left, right, bottom, top
+    int side_kind[4] = {LBM_SIDE_DIFFUSE, LBM_SIDE_DIFFUSE, LBM_SIDE_DIFFUSE, LBM_SIDE_DIFFUSE};
+    double side_val[4] = {0.0, 0.0, 0.0, 0.0};
     double tau_N = 0.0, tau_R = 0.0, tau = 0.0, tau_r = 0.0, kappa = 1.0, sigma = 0.0;
     int precision = 0;
     double e_ref = 1.0;
@@ -108,7 +111,7 @@ struct DeviceGuard {
 template <typename C>
 Coef<C> make_coef(const lbm_ctx *c) {
     // Eqs. 13, 15-18, 54 and 58 as the coefficients of lbm_device.cuh.
-    Coef<C> k;
+    Coef<C> k{};
     k.omega = (C)(1.0 / c->tau);
     k.sigma = (C)c->sigma;
     k.lambda = (C)(std::isinf(c->tau_r) ? 0.0 : 1.0 / (2.0 * c->tau_r + 1.0));
@@ -120,7 +123,49 @@ Coef<C> make_coef(const lbm_ctx *c) {
     k.u_diag = ((C)1 - k.u_axis) / (C)2;            // exact: u_axis + 2 u_diag = 1
     k.jump_axis = (C)(c->scale * (2.0 / 9.0) * c->delta_e);
     k.jump_diag = (C)(c->scale * (1.0 / 36.0) * c->delta_e);
+    // Eq. 55 on deviations: s w_i (e_s - e_ref); Eq. 57: s q_0 / kappa
+    for (int sd = 0; sd < 4; ++sd) {
+        const int kind = c->side_kind[sd];
+        const double v = c->side_val[sd];
+        k.side_kind[sd] = kind;
+        k.side_axis[sd] = (C)(kind == LBM_SIDE_ISOTHERMAL ? c->scale * (2.0 / 9.0) * (v - c->e_ref)
+                                                          : 0.0);
+        k.side_diag[sd] = (C)(kind == LBM_SIDE_ISOTHERMAL ? c->scale * (1.0 / 36.0) * (v - c->e_ref)
+                                                          : 0.0);
+        k.side_flux[sd] = (C)(kind == LBM_SIDE_HEAT_FLUX ? c->scale * v / c->kappa : 0.0);
+    }
     return k;
+}
+
+bool has_sides(const lbm_ctx *c) { return c->bc_x == LBM_BC_SIDES || c->bc_y == LBM_BC_SIDES; }
+
+// Largest |d_i| / s a side can write: w_axis |e_s - e_ref| for an isothermal
+// side, about |q_0| / kappa for a heat-flux side.
+double side_bound(const lbm_ctx *c, int kind, double v) {
+    if (kind == LBM_SIDE_ISOTHERMAL) return (2.0 / 9.0) * std::fabs(v - c->e_ref);
+    if (kind == LBM_SIDE_HEAT_FLUX) return std::fabs(v) / c->kappa;
+    return 0.0;
+}
+
+// A corner node between a BC_SIDES x side and a y side (walls or a side)
+// receives unknown populations from both directions; the scheme fixes them
+// only when one of its sides is isothermal (Eq. 55 sets the whole node).
+lbm_status check_corners(lbm_ctx *c) {
+    if (c->bc_x != LBM_BC_SIDES ||
+        (c->bc_y != LBM_BC_SIDES && c->bc_y != LBM_BC_DIFFUSE_WALLS))
+        return LBM_OK;
+    static const char *xname[2] = {"left", "right"}, *yname[2] = {"bottom", "top"};
+    for (int xs = 0; xs < 2; ++xs)
+        for (int ys = 0; ys < 2; ++ys) {
+            const bool iso = c->side_kind[xs] == LBM_SIDE_ISOTHERMAL ||
+                             (c->bc_y == LBM_BC_SIDES && c->side_kind[2 + ys] == LBM_SIDE_ISOTHERMAL);
+            if (!iso)
+                return fail(c, LBM_EUNSUPPORTED,
+                            std::string("the ") + xname[xs] + "-" + yname[ys] +
+                                " corner touches no isothermal side; the scheme defines no "
+                                "treatment for it");
+        }
+    return LBM_OK;
 }
 
 Readout make_readout(const lbm_ctx *c) {
@@ -222,7 +267,7 @@ lbm_status ensure_scratch(lbm_ctx *c, bool need_prev) {
     }
     if (need_prev) {
         long long blocks = step_blocks(c->kernel, c->precision, c->nx, c->ny, c->plan);
-        const long long rb = readout_blocks(c->precision, c->nx, c->ny);
+        const long long rb = readout_blocks(c->precision, c->nx, c->ny, c->bc_x, c->bc_y);
         if (blocks < rb) blocks = rb;
         if (blocks > c->partial_blocks) {
             cudaFree(c->partials);
@@ -269,6 +314,8 @@ lbm_status finish_residual(lbm_ctx *c, const double (&sums)[5], double *r,
 }
 
 int resolve_kernel(lbm_ctx *c, int requested) {
+    if (has_sides(c))       // only the scalar pull applies the per-side rules
+        return (requested == KERNEL_AUTO || requested == KERNEL_SCALAR) ? KERNEL_SCALAR : -1;
     const bool vec_ok = c->nx % vector_width(c->precision) == 0;
     // the staged kernel also needs its plan (launch attributes, occupancy)
     // worked out on this device, here, outside any stream capture
@@ -303,11 +350,13 @@ lbm_status create_common(lbm_grid g, double tau_N, double tau_R, lbm_boundary bc
     if (bc.y == LBM_BC_PERIODIC_GRADIENT)
         return fail(nullptr, LBM_EUNSUPPORTED,
                     "the periodic temperature gradient is supported on x only");
-    if ((bc.x != LBM_BC_PERIODIC && bc.x != LBM_BC_PERIODIC_GRADIENT) ||
-        (bc.y != LBM_BC_PERIODIC && bc.y != LBM_BC_DIFFUSE_WALLS))
+    if ((bc.x != LBM_BC_PERIODIC && bc.x != LBM_BC_PERIODIC_GRADIENT && bc.x != LBM_BC_SIDES) ||
+        (bc.y != LBM_BC_PERIODIC && bc.y != LBM_BC_DIFFUSE_WALLS && bc.y != LBM_BC_SIDES))
         return fail(nullptr, LBM_EINVAL, "unknown boundary kind");
     if (bc.y == LBM_BC_DIFFUSE_WALLS && g.ny < 2)
         return fail(nullptr, LBM_EINVAL, "diffuse walls need ny >= 2");
+    if ((bc.x == LBM_BC_SIDES && g.nx < 2) || (bc.y == LBM_BC_SIDES && g.ny < 2))
+        return fail(nullptr, LBM_EINVAL, "a direction with two sides needs at least 2 nodes");
     if (!std::isfinite(bc.delta_e)) return fail(nullptr, LBM_EINVAL, "delta_e is not finite");
     if (!std::isfinite(e_ref)) return fail(nullptr, LBM_EINVAL, "e_ref is not finite");
     if (std::isnan(tau_N) || std::isnan(tau_R) || !(tau_N > 0.0) || !(tau_R > 0.0))
@@ -398,7 +447,10 @@ lbm_status init_from_device(lbm_ctx *c, const double *e, const double *qx, const
     if (c->precision == PREC_FP16 || c->precision == PREC_BF16) {
         // largest |d_i| ~ 2^12 after scaling: room for 16x growth below the
         // FP16 maximum, far above its smallest normal number
-        const double a = std::fmax(amax, (2.0 / 9.0) * std::fabs(c->delta_e));
+        double a = std::fmax(amax, (2.0 / 9.0) * std::fabs(c->delta_e));
+        if (has_sides(c))
+            for (int sd = 0; sd < 4; ++sd)
+                a = std::fmax(a, side_bound(c, c->side_kind[sd], c->side_val[sd]));
         if (a > 0.0) {
             int ex;
             std::frexp(a, &ex);        // a < 2^ex
@@ -513,6 +565,7 @@ lbm_status lbm_step(lbm_ctx *c, long n) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    if (lbm_status s = check_corners(c)) return s;
     DeviceGuard g(c->device);
     long left = n;
     if (c->graph_chunk > 0 && left >= c->graph_chunk) {
@@ -545,6 +598,8 @@ lbm_status lbm_sync(lbm_ctx *c) {
 lbm_status lbm_moments_device(lbm_ctx *c, double *e, double *qx, double *qy) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    if (c->n > 0)
+        if (lbm_status s = check_corners(c)) return s;
     DeviceGuard g(c->device);
     if (!e && !qx && !qy) return LBM_OK;
     CK(c, dispatch<MomentsOp>(c, e, qx, qy));
@@ -554,6 +609,8 @@ lbm_status lbm_moments_device(lbm_ctx *c, double *e, double *qx, double *qy) {
 lbm_status lbm_moments(lbm_ctx *c, double *e, double *qx, double *qy) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    if (c->n > 0)
+        if (lbm_status s = check_corners(c)) return s;
     DeviceGuard g(c->device);
     if (!e && !qx && !qy) return LBM_OK;
     if (lbm_status s = ensure_scratch(c, false)) return s;
@@ -573,6 +630,8 @@ lbm_status lbm_populations(lbm_ctx *c, double *f) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!f) return fail(c, LBM_EINVAL, "f is NULL");
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    if (c->n > 0)
+        if (lbm_status s = check_corners(c)) return s;
     DeviceGuard g(c->device);
     double *dev = nullptr;
     CK(c, cudaMallocAsync((void **)&dev, sizeof(double) * 8 * (size_t)c->plane, c->stream));
@@ -589,6 +648,8 @@ lbm_status lbm_populations(lbm_ctx *c, double *f) {
 lbm_status lbm_residual(lbm_ctx *c, double *r, double *total_energy) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    if (c->n > 0)
+        if (lbm_status s = check_corners(c)) return s;
     DeviceGuard g(c->device);
     if (lbm_status s = ensure_scratch(c, true)) return s;
     CK(c, dispatch<ResidualOp>(c, 0));
@@ -603,6 +664,8 @@ lbm_status lbm_step_residual(lbm_ctx *c, long n, double *r, double *total_energy
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
+    if (c->n > 0)
+        if (lbm_status s = check_corners(c)) return s;
     if (n == 0) return lbm_residual(c, r, total_energy);
     DeviceGuard g(c->device);
     if (lbm_status s = ensure_scratch(c, true)) return s;
@@ -699,6 +762,38 @@ lbm_status lbm_set_kernel(lbm_ctx *c, int kernel) {
 
 int lbm_get_kernel(const lbm_ctx *c) { return c ? c->kernel : -1; }
 
+lbm_status lbm_set_side(lbm_ctx *c, int side, int kind, double value) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (side < LBM_SIDE_LEFT || side > LBM_SIDE_TOP) return fail(c, LBM_EINVAL, "unknown side");
+    if (kind < LBM_SIDE_DIFFUSE || kind > LBM_SIDE_HEAT_FLUX)
+        return fail(c, LBM_EINVAL, "unknown side treatment");
+    if ((side <= LBM_SIDE_RIGHT ? c->bc_x : c->bc_y) != LBM_BC_SIDES)
+        return fail(c, LBM_EINVAL, "the side's direction was not created with LBM_BC_SIDES");
+    if (!std::isfinite(value)) return fail(c, LBM_EINVAL, "side value is not finite");
+    if (kind == LBM_SIDE_DIFFUSE) value = 0.0;
+    if (c->initialised && (c->precision == PREC_FP16 || c->precision == PREC_BF16) &&
+        side_bound(c, kind, value) * c->scale > 32768.0)
+        return fail(c, LBM_EINVAL,
+                    "side value too large for the 16-bit storage scale fixed at lbm_init; "
+                    "set the sides before lbm_init");
+    if (kind != c->side_kind[side] || value != c->side_val[side]) {
+        DeviceGuard g(c->device);
+        drop_graphs(c);       // captured launches hold the old coefficients
+        c->side_kind[side] = kind;
+        c->side_val[side] = value;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_side(const lbm_ctx *c, int side, int *kind, double *value) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (side < LBM_SIDE_LEFT || side > LBM_SIDE_TOP)
+        return fail(const_cast<lbm_ctx *>(c), LBM_EINVAL, "unknown side");
+    if (kind) *kind = c->side_kind[side];
+    if (value) *value = c->side_val[side];
+    return LBM_OK;
+}
+
 lbm_status lbm_set_staged_config(lbm_ctx *c, int stages, int ctas_per_sm, int consumer_warps,
                                  int l2_evict_first) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
@@ -755,10 +850,11 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
     struct Cand { int kernel, stages, cw; };
     Cand cands[8];
     int nc = 0;
-    if (c->nx % vector_width(c->precision) == 0) cands[nc++] = {KERNEL_VECTOR, 0, 0};
+    const bool sides = has_sides(c);      // the per-side rules run on the scalar kernel only
+    if (!sides && c->nx % vector_width(c->precision) == 0) cands[nc++] = {KERNEL_VECTOR, 0, 0};
     else cands[nc++] = {KERNEL_SCALAR, 0, 0};
     for (int cw : {8, 4})
-        if (staged_supported(c->precision, c->nx, c->ny, cw))
+        if (!sides && staged_supported(c->precision, c->nx, c->ny, cw))
             for (int st : {2, 3}) cands[nc++] = {KERNEL_STAGED, st, cw};
 
     // keep the state: copy both buffers aside when the lattice holds one

@@ -18,7 +18,9 @@ __host__ __device__ constexpr int cy_of(int i) {
     return (i == 1 || i == 4 || i == 5) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
 }
 
-enum { BC_PERIODIC = 0, BC_GRADIENT = 1, BC_WALLS = 2 };
+enum { BC_PERIODIC = 0, BC_GRADIENT = 1, BC_WALLS = 2, BC_SIDES = 3 };
+// Treatments of the sides of a BC_SIDES direction (Section 2.5).
+enum { SIDE_DIFFUSE = 0, SIDE_ISOTHERMAL = 1, SIDE_HEAT_FLUX = 2 };
 
 // Coefficients of the collision, computed on the host in FP64 and rounded
 // once to the compute type C.  On deviations d_i (scaled by s), with
@@ -42,6 +44,11 @@ struct Coef {
     C h_axis, h_diag;         // (5/3) a_i, Eq. 18
     C u_axis, u_diag;         // Eq. 58: w_i / (5/18) = 4/5 and 1/10
     C jump_axis, jump_diag;   // s w_i delta_e, Eqs. 59-60
+    // Sides of BC_SIDES directions, in the order left, right, bottom, top.
+    int side_kind[4];         // SIDE_*
+    C side_axis[4];           // isothermal: s w_i (e_s - e_ref), Eq. 55
+    C side_diag[4];
+    C side_flux[4];           // heat flux: s q_0 (2 tau_r + 1)/(2 tau_r), Eq. 57
 };
 
 // Storage traits: how a population plane element is stored and converted.
@@ -109,10 +116,59 @@ __device__ __forceinline__ void wall_top(C (&d)[8], const Coef<C> &k) {
     d[7] = k.u_diag * s;
 }
 
+// Section 2.5 on a node of the sides of BC_SIDES directions, after the
+// pull (unknown populations are 0 in d).  on_* tell which sides the node
+// lies on.  A node on an isothermal side is set to the equilibrium at rest
+// at e_s (Eq. 55; the first isothermal side in the order left, right,
+// bottom, top when two meet at a corner).  Otherwise each of its sides, in
+// the order bottom, top, left, right, sets its unknown populations
+// (c_i . n < 0) to w_i / (5/18) times the sum of the incident ones
+// (c_i . n > 0) plus s q_0 / kappa (Eq. 57; Eq. 58 when q_0 = 0).
+template <typename C>
+__device__ __forceinline__ void apply_sides(C (&d)[8], const Coef<C> &k, bool on_left,
+                                            bool on_right, bool on_bottom, bool on_top) {
+    bool iso = false;
+    C va = C(0), vd = C(0);
+    // later assignments win, so the first isothermal side in order is kept
+    if (on_top && k.side_kind[3] == SIDE_ISOTHERMAL) { iso = true; va = k.side_axis[3]; vd = k.side_diag[3]; }
+    if (on_bottom && k.side_kind[2] == SIDE_ISOTHERMAL) { iso = true; va = k.side_axis[2]; vd = k.side_diag[2]; }
+    if (on_right && k.side_kind[1] == SIDE_ISOTHERMAL) { iso = true; va = k.side_axis[1]; vd = k.side_diag[1]; }
+    if (on_left && k.side_kind[0] == SIDE_ISOTHERMAL) { iso = true; va = k.side_axis[0]; vd = k.side_diag[0]; }
+    if (iso) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) d[i] = i < 4 ? va : vd;
+        return;
+    }
+    if (on_bottom) {          // n = (0,-1): unknown 1,4,5; incident 3,6,7
+        const C s = (d[3] + d[6] + d[7]) + k.side_flux[2];
+        d[1] = k.u_axis * s;
+        d[4] = k.u_diag * s;
+        d[5] = k.u_diag * s;
+    }
+    if (on_top) {             // n = (0,1): unknown 3,6,7; incident 1,4,5
+        const C s = (d[1] + d[4] + d[5]) + k.side_flux[3];
+        d[3] = k.u_axis * s;
+        d[6] = k.u_diag * s;
+        d[7] = k.u_diag * s;
+    }
+    if (on_left) {            // n = (-1,0): unknown 0,4,7; incident 2,5,6
+        const C s = (d[2] + d[5] + d[6]) + k.side_flux[0];
+        d[0] = k.u_axis * s;
+        d[4] = k.u_diag * s;
+        d[7] = k.u_diag * s;
+    }
+    if (on_right) {           // n = (1,0): unknown 2,5,6; incident 0,4,7
+        const C s = (d[0] + d[4] + d[7]) + k.side_flux[1];
+        d[2] = k.u_axis * s;
+        d[5] = k.u_diag * s;
+        d[6] = k.u_diag * s;
+    }
+}
+
 // Generic pull of the 8 populations arriving at node (x, y) at the next
 // step from the post-collision planes `src` (one node, any nx).  Applies the
-// seam jump and the walls.  Used by the scalar step kernel and by every
-// read-out kernel.
+// seam jump, the walls and the per-side treatments.  Used by the scalar step
+// kernel and by every read-out kernel.
 template <typename T>
 __device__ __forceinline__ void pull_node(const T *__restrict__ src, long long plane,
                                           int nx, int ny, int x, int y, int bc_x,
@@ -120,16 +176,22 @@ __device__ __forceinline__ void pull_node(const T *__restrict__ src, long long p
                                           typename Store<T>::C (&d)[8]) {
     using C = typename Store<T>::C;
     const bool walls = bc_y == BC_WALLS;
+    const bool sides_x = bc_x == BC_SIDES, sides_y = bc_y == BC_SIDES;
+    const bool open_y = walls || sides_y;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int cx = cx_of(i), cy = cy_of(i);
         int sy = y - cy;
-        if (walls && (sy < 0 || sy >= ny)) {
-            d[i] = C(0);          // unknown: filled by Eq. 58 below
+        if (open_y && (sy < 0 || sy >= ny)) {
+            d[i] = C(0);          // unknown: filled by Eq. 58 / the sides below
             continue;
         }
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
         int sx = x - cx;
+        if (sides_x && (sx < 0 || sx >= nx)) {
+            d[i] = C(0);          // unknown: filled by the x sides below
+            continue;
+        }
         C jump = C(0);
         if (sx < 0) {             // crossed the seam moving right (Eq. 59)
             sx += nx;
@@ -144,6 +206,9 @@ __device__ __forceinline__ void pull_node(const T *__restrict__ src, long long p
         if (y == 0) wall_bottom(d, k);
         if (y == ny - 1) wall_top(d, k);
     }
+    if (sides_x || sides_y)
+        apply_sides(d, k, sides_x && x == 0, sides_x && x == nx - 1, sides_y && y == 0,
+                    sides_y && y == ny - 1);
 }
 
 // Residual contribution of one node of the state at step n (pulled, after

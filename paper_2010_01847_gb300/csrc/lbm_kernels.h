@@ -56,7 +56,7 @@ cudaError_t launch_step_staged(const T *src, T *dst, int nx, int ny, int bc_x, i
 bool staged_supported(int precision, int nx, int ny, int consumer_warps);
 
 // Blocks of the stand-alone residual pass (sizes its per-block partials).
-long long readout_blocks(int precision, int nx, int ny);
+long long readout_blocks(int precision, int nx, int ny, int bc_x, int bc_y);
 
 // Fixed-order sum of per-block partials (5 doubles each) into sums[0..4].
 cudaError_t launch_finalize(const double *partials, int blocks, double *sums,

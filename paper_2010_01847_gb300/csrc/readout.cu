@@ -149,13 +149,31 @@ __global__ void populations_kernel(const T *__restrict__ src, Readout r,
     }
 }
 
-// Fixed-order sum of the per-block partials (deterministic result).
-__global__ void __launch_bounds__(256) finalize_sums(const double *__restrict__ partials,
-                                                     int blocks, double *__restrict__ sums) {
+// Fixed-order sum of the per-block partials (deterministic result).  One
+// block of FINALIZE_THREADS; each thread sums every FINALIZE_THREADS-th
+// record, four records per iteration so that enough loads are in flight for
+// one SM to stream the ~2.6 MB of partials of an 8192^2 lattice.
+constexpr int FINALIZE_THREADS = 1024;
+
+__global__ void __launch_bounds__(FINALIZE_THREADS)
+finalize_sums(const double *__restrict__ partials, int blocks, double *__restrict__ sums) {
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < blocks; b += blockDim.x) {
+    const int stride = FINALIZE_THREADS;
+    int b = threadIdx.x;
+    for (; b + 3 * stride < blocks; b += 4 * stride) {
+        double v[4][5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) acc[q] += partials[b * 5 + q];
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) v[u][q] = partials[(size_t)(b + u * stride) * 5 + q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) acc[q] += v[u][q];
+    }
+    for (; b < blocks; b += stride) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[q] += partials[(size_t)b * 5 + q];
     }
     block_sum5_store(acc, sums);
 }
@@ -219,17 +237,25 @@ static unsigned grid_for(long long n, int threads) {
     return (unsigned)(b > 0 ? b : 1);
 }
 
-template <typename T> static bool vec_ok(const Readout &r) { return r.nx % Pack<T>::V == 0; }
+// the vectorised pull knows the periodic, seam and wall rules but not the
+// per-side treatments of BC_SIDES directions
+static bool vector_readout(int precision_width, int nx, int bc_x, int bc_y) {
+    return nx % precision_width == 0 && bc_x != BC_SIDES && bc_y != BC_SIDES;
+}
+
+template <typename T> static bool vec_ok(const Readout &r) {
+    return vector_readout(Pack<T>::V, r.nx, r.bc_x, r.bc_y);
+}
 
 template <typename T> static unsigned vec_blocks(const Readout &r) {
     const long long threads = (long long)r.nx * r.ny / Pack<T>::V;
     return (unsigned)((threads + 255) / 256);
 }
 
-long long readout_blocks(int precision, int nx, int ny) {
+long long readout_blocks(int precision, int nx, int ny, int bc_x, int bc_y) {
     const long long plane = (long long)nx * ny;
     const int v = vector_width(precision);
-    if (nx % v) return RESIDUAL_BLOCKS;
+    if (!vector_readout(v, nx, bc_x, bc_y)) return RESIDUAL_BLOCKS;
     return (plane / v + 255) / 256;
 }
 
@@ -275,7 +301,7 @@ cudaError_t launch_residual(const T *src, const Readout &r, const Coef<typename 
 
 cudaError_t launch_finalize(const double *partials, int blocks, double *sums,
                             cudaStream_t stream) {
-    finalize_sums<<<1, 256, 0, stream>>>(partials, blocks, sums);
+    finalize_sums<<<1, FINALIZE_THREADS, 0, stream>>>(partials, blocks, sums);
     return cudaGetLastError();
 }
 
