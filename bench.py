@@ -89,6 +89,22 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(value, dist=None, device=None):
+    """The job's time: the maximum of a per-rank value over all ranks (the
+    slowest replica sets it); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_value(world, sites, steps, seconds):
+    """Whole-job GLUPS: site updates of all ranks over the job's time."""
+    return world * sites * steps / seconds / 1e9
+
+
 def workload(args):
     w = inputs.THROUGHPUT_8192
     return dict(nx=args.nx, ny=args.ny, kn_N=w.kn_N, kn_R=w.kn_R, length=w.length)
@@ -349,12 +365,9 @@ def run_native(args):
     elapsed = t0.elapsed_time(t1) / 1e3
     kern_s = sum(a.elapsed_time(b) for a, b, _ in events) / 1e3
     kern_steps = sum(k for _, _, k in events)
-    if dist:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = t.item()
+    elapsed = max_over_ranks(elapsed, dist, dev)
     sites = nx * ny
-    value = world * sites * args.steps / elapsed / 1e9
+    value = job_value(world, sites, args.steps, elapsed)
 
     # roofline of the stream-collide kernel
     bps = 16 * STORAGE_BYTES[args.precision]
@@ -385,11 +398,8 @@ def run_native(args):
         for dst, src in zip(op, m):
             dst[...] = src
         t_e2e = time.perf_counter() - t_start
-        if dist:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = t.item()
-        e2e = {"value": world * sites * args.steps / t_e2e / 1e9, "unit": "GLUPS",
+        t_e2e = max_over_ranks(t_e2e, dist, dev)
+        e2e = {"value": job_value(world, sites, args.steps, t_e2e), "unit": "GLUPS",
                "h2d_bytes_per_step": 3 * 8 * sites / args.steps,
                "d2h_bytes_per_step": 3 * 8 * sites / args.steps,
                "what": "lbm_init from pinned host (e, qx, qy) + steps + lbm_moments to host"}

@@ -469,6 +469,20 @@ lbm_status lbm_residual_noalloc(const double *e, const double *qx, const double 
                                 const double *prev_qy, long long n_nodes, double e_ref,
                                 long k_steps, void *stream, double *r, double *total_energy);
 
+/* Self-check of the failure path of the staged kernel's waits (no
+ * counterpart in the paper).  Every mbarrier wait in the staged kernel is
+ * bounded by an iteration count and a clock limit (about 2 s); when it gives
+ * up it sets the context's status word, which the next synchronising call
+ * reports as LBM_ETIMEOUT, and the CTA drains its copies and exits, so the
+ * CUDA context stays usable.  This call runs that same wait, in one thread
+ * of one CTA, on a fresh barrier that nothing completes, on `stream`
+ * (cudaStream_t, NULL = legacy default) of the current device, and waits
+ * for it: *gave_up = 1 when the wait ended by its limit and set the status
+ * word, *seconds = the kernel's duration (either pointer may be NULL).
+ * Allocates 4 bytes of device memory for the duration of the call.
+ * Errors: ECUDA (text from lbm_last_error(NULL)). */
+lbm_status lbm_check_bounded_wait(void *stream, int *gave_up, double *seconds);
+
 /* ------------------------------------------------------------------------ *
  * The D1Q2 and D3Q14 lattices (periodic lattices only).
  *

@@ -51,7 +51,7 @@ EXPORTS = [
     "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_param_count", "lbm_mlp_set_params",
     "lbm_mlp_get_params", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train_step",
     "lbm_mlp_last_error",
-    "lbm_residual_noalloc",
+    "lbm_residual_noalloc", "lbm_check_bounded_wait",
     "lbm_nd_lattice_speed", "lbm_nd_create", "lbm_nd_init", "lbm_nd_step", "lbm_nd_sync",
     "lbm_nd_moments", "lbm_nd_populations", "lbm_nd_energy", "lbm_nd_step_count",
     "lbm_nd_destroy", "lbm_nd_last_error",
@@ -156,6 +156,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_mlp_last_error": (ctypes.c_char_p, [vp]),
         "lbm_residual_noalloc": (st, [vp, vp, vp, vp, vp, vp, ctypes.c_longlong,
                                       ctypes.c_double, c_long, vp, dp, dp]),
+        "lbm_check_bounded_wait": (st, [vp, ctypes.POINTER(ctypes.c_int), dp]),
         "lbm_nd_lattice_speed": (ctypes.c_double, [ctypes.c_int]),
         "lbm_nd_create": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
@@ -202,6 +203,20 @@ def residual_noalloc(fields, prev_fields=None, k_steps=0, e_ref=1.0, stream=None
     if st != OK:
         raise LBMError(st, lib.lbm_last_error(None).decode())
     return r.value, en.value
+
+
+def check_bounded_wait(stream=None):
+    """lbm_check_bounded_wait: (gave_up, seconds) of the staged kernel's
+    bounded mbarrier wait run against a barrier nothing completes."""
+    lib = load_library()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    g, sec = ctypes.c_int(), ctypes.c_double()
+    st = lib.lbm_check_bounded_wait(ctypes.c_void_p(stream), ctypes.byref(g), ctypes.byref(sec))
+    if st != OK:
+        raise LBMError(st, lib.lbm_last_error(None).decode())
+    return bool(g.value), sec.value
 
 
 def _dptr(a: np.ndarray):

@@ -589,6 +589,7 @@ void lbm_batch_destroy(lbm_batch *b) {
 }
 
 lbm_status lbm_batch_init(lbm_batch *b, const double *e, const double *qx, const double *qy) {
+    NvtxRange nvtx_("lbm_batch_init");
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     BGuard g(b->device);
     drop_graph(b);
@@ -684,6 +685,7 @@ lbm_status lbm_batch_init(lbm_batch *b, const double *e, const double *qx, const
 }
 
 lbm_status lbm_batch_step(lbm_batch *b, long n) {
+    NvtxRange nvtx_("lbm_batch_step");
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     if (n < 0) return bfail(b, LBM_EINVAL, "n must be >= 0");
     if (!b->initialised) return bfail(b, LBM_EINVAL, "lbm_batch_init has not been called");
@@ -733,6 +735,7 @@ lbm_status lbm_batch_residuals(lbm_batch *b, double *r, double *energy) {
 
 lbm_status lbm_batch_solve(lbm_batch *b, double tol, int check_every, long max_steps,
                            long *steps, double *r) {
+    NvtxRange nvtx_("lbm_batch_solve");
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     if (!b->initialised) return bfail(b, LBM_EINVAL, "lbm_batch_init has not been called");
     if (!(tol > 0.0)) return bfail(b, LBM_EINVAL, "tol must be > 0");
@@ -901,6 +904,7 @@ lbm_status lbm_batch_get_schedule(const lbm_batch *b, int *threads_per_item, int
 }
 
 lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, double *us_per_step) {
+    NvtxRange nvtx_("lbm_batch_autotune");
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     if (!b->initialised) return bfail(b, LBM_EINVAL, "lbm_batch_init has not been called");
     if (trial_steps < 0) return bfail(b, LBM_EINVAL, "trial_steps must be >= 0");

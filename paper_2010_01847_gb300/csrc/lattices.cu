@@ -520,6 +520,7 @@ static lbm_status nd_scratch(lbm_nd *c) {
 }
 
 lbm_status lbm_nd_init(lbm_nd *c, const double *e, const double *q) {
+    NvtxRange nvtx_("lbm_nd_init");
     if (!c) return nd_fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!e) return nd_fail(c, LBM_EINVAL, "e is NULL");
     NdDevice g(c->device);
@@ -545,6 +546,7 @@ lbm_status lbm_nd_init(lbm_nd *c, const double *e, const double *q) {
 }
 
 lbm_status lbm_nd_step(lbm_nd *c, long n) {
+    NvtxRange nvtx_("lbm_nd_step");
     if (!c) return nd_fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (n < 0) return nd_fail(c, LBM_EINVAL, "n must be >= 0");
     if (!c->initialised) return nd_fail(c, LBM_EINVAL, "lbm_nd_init has not been called");

@@ -539,6 +539,7 @@ void lbm_destroy(lbm_ctx *c) {
 }
 
 lbm_status lbm_init(lbm_ctx *c, const double *e, const double *qx, const double *qy) {
+    NvtxRange nvtx_("lbm_init");
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!e) return fail(c, LBM_EINVAL, "e is NULL");
     DeviceGuard g(c->device);
@@ -562,6 +563,7 @@ lbm_status lbm_init_device(lbm_ctx *c, const double *e, const double *qx, const 
 }
 
 lbm_status lbm_step(lbm_ctx *c, long n) {
+    NvtxRange nvtx_("lbm_step");
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
@@ -607,6 +609,7 @@ lbm_status lbm_moments_device(lbm_ctx *c, double *e, double *qx, double *qy) {
 }
 
 lbm_status lbm_moments(lbm_ctx *c, double *e, double *qx, double *qy) {
+    NvtxRange nvtx_("lbm_moments");
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
     if (c->n > 0)
@@ -646,6 +649,7 @@ lbm_status lbm_populations(lbm_ctx *c, double *f) {
 }
 
 lbm_status lbm_residual(lbm_ctx *c, double *r, double *total_energy) {
+    NvtxRange nvtx_("lbm_residual");
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
     if (c->n > 0)
@@ -661,6 +665,7 @@ lbm_status lbm_residual(lbm_ctx *c, double *r, double *total_energy) {
 }
 
 lbm_status lbm_step_residual(lbm_ctx *c, long n, double *r, double *total_energy) {
+    NvtxRange nvtx_("lbm_step_residual");
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
@@ -841,6 +846,7 @@ lbm_status lbm_set_graph_chunk(lbm_ctx *c, int steps) {
 }
 
 lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per_step) {
+    NvtxRange nvtx_("lbm_autotune");
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (trial_steps < 0) return fail(c, LBM_EINVAL, "trial_steps must be >= 0");
     if (trial_steps == 0) trial_steps = 20;
@@ -924,6 +930,32 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
     }
     if (kernel) *kernel = c->kernel;
     if (us_per_step) *us_per_step = 1000.0 * best / trial_steps;
+    return LBM_OK;
+}
+
+lbm_status lbm_check_bounded_wait(void *stream, int *gave_up, double *seconds) {
+    if (gave_up) *gave_up = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *status = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaMalloc(&status, sizeof(int));
+    if (err == cudaSuccess) err = cudaMemsetAsync(status, 0, sizeof(int), s);
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+    if (err == cudaSuccess) err = launch_wait_probe(status, s);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    int st = 0;
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(status);
+    if (err != cudaSuccess) return cuda_fail(nullptr, err, "lbm_check_bounded_wait");
+    if (gave_up) *gave_up = st != 0;
+    if (seconds) *seconds = ms / 1e3;
     return LBM_OK;
 }
 

@@ -2,10 +2,20 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "lbm_device.cuh"
 
 namespace plbm {
+
+// Names a host-side call on profiler timelines (NVTX range; costs nothing
+// when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 enum { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2, PREC_FP64 = 3 };
 enum { KERNEL_AUTO = 0, KERNEL_SCALAR = 1, KERNEL_VECTOR = 2, KERNEL_STAGED = 3 };
@@ -54,6 +64,10 @@ cudaError_t launch_step_staged(const T *src, T *dst, int nx, int ny, int bc_x, i
                                const Coef<typename Store<T>::C> &k, int *status,
                                const StagedPlan &plan, int *blocks_out, cudaStream_t stream);
 bool staged_supported(int precision, int nx, int ny, int consumer_warps);
+
+// Runs the staged kernel's bounded mbarrier wait against a barrier nothing
+// completes (one CTA, ~2 s); the wait gives up and ORs 1 into *status.
+cudaError_t launch_wait_probe(int *status, cudaStream_t stream);
 
 // Blocks of the stand-alone residual pass (sizes its per-block partials).
 long long readout_blocks(int precision, int nx, int ny, int bc_x, int bc_y);

@@ -379,6 +379,7 @@ lbm_status lbm_mlp_get_params(lbm_mlp *m, float *host) {
 }
 
 lbm_status lbm_mlp_forward(lbm_mlp *m, const float *x, int batch, float *y) {
+    NvtxRange nvtx_("lbm_mlp_forward");
     if (!m || !x || !y) return mfail(m, LBM_EINVAL, "NULL argument");
     if (batch < 1 || batch > m->max_batch) return mfail(m, LBM_EINVAL, "batch out of range");
     MCK(m, forward(m, x, batch));
@@ -438,6 +439,7 @@ lbm_status lbm_mlp_loss_grad(lbm_mlp *m, const float *x, const float *t, int bat
 
 lbm_status lbm_mlp_train_step(lbm_mlp *m, const float *x, const float *t, int batch, float lr,
                               double *loss) {
+    NvtxRange nvtx_("lbm_mlp_train_step");
     if (!m || !x || !t) return mfail(m, LBM_EINVAL, "NULL argument");
     if (batch < 1 || batch > m->max_batch) return mfail(m, LBM_EINVAL, "batch out of range");
     if (!(lr > 0.f)) return mfail(m, LBM_EINVAL, "lr must be > 0");

@@ -426,6 +426,24 @@ cudaError_t launch_step_staged(const T *src, T *dst, int nx, int ny, int bc_x, i
     return launch_cw<T, 8>(src, dst, nx, ny, bc_x, bc_y, k, status, plan, blocks_out, stream);
 }
 
+// One thread waits, with the kernel's bounded wait, on a fresh mbarrier
+// that no thread ever arrives at: the wait gives up after its clock limit
+// (about 2 s) and sets *status, exactly as a stalled pipeline stage would.
+__global__ void wait_probe(int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0u, status);
+}
+
+cudaError_t launch_wait_probe(int *status, cudaStream_t stream) {
+    wait_probe<<<1, 32, 0, stream>>>(status);
+    return cudaGetLastError();
+}
+
 #define PLBM_STAGED(T)                                                                       \
     template cudaError_t launch_step_staged<T>(const T *, T *, int, int, int, int,           \
                                                const Coef<Store<T>::C> &, int *,             \

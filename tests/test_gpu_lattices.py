@@ -27,11 +27,12 @@ def _fields(L, shape, seed):
     return e, q
 
 
-def _errs(gpu, orc):
+def _errs(gpu, orc, scale_e, scale_q):
+    """Largest errors of e and q relative to the size of the input's
+    deviations (small lattices relax to uniform within the run, so the
+    current spread is no scale)."""
     (eg, qg), (eo, qo) = gpu, orc
-    err_e = np.abs(eg - eo).max() / np.abs(eo - eo.mean()).max()
-    err_q = np.abs(qg - qo).max() / np.abs(qo).max()
-    return err_e, err_q
+    return np.abs(eg - eo).max() / scale_e, np.abs(qg - qo).max() / scale_q
 
 
 CASES = [
@@ -56,14 +57,17 @@ def test_nd_parity(case, precision):
     o = lt.Run(L, shape, tau_N, tau_R)
     o.init(e, q)
     tol = TOL[precision]
+    scale_e, scale_q = np.abs(e - 1.0).max(), np.abs(q).max()
+    scale_f = np.abs(o.f - L.w.reshape((L.Q,) + (1,) * L.dim)).max()
     for steps in (0, 1, 70):               # 70: one 64-step graph plus single steps
         g.step(steps - g.step_count)
         o.step(steps - o.step_count)
-        err_e, err_q = _errs(g.moments(), o.moments())
+        err_e, err_q = _errs(g.moments(), o.moments(), scale_e, scale_q)
         assert err_e <= tol and err_q <= tol, (steps, err_e, err_q)
-        dev = np.abs(o.f - L.w.reshape((L.Q,) + (1,) * L.dim) * o.f.sum(0).mean()).max()
-        assert np.abs(g.populations() - o.f).max() / dev <= tol
-    assert g.energy() == pytest.approx(o.f.sum(), rel=1e-12)
+        assert np.abs(g.populations() - o.f).max() / scale_f <= tol
+    # total energy: the deviation sum, to the storage's precision
+    n = int(np.prod(shape))
+    assert abs((g.energy() - n) - (o.f.sum() - n)) <= tol * np.abs(e - 1.0).sum()
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-4)])

