@@ -64,11 +64,13 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="heat_mode",
-                    choices=["heat_mode", "batch", "warmstart", "d3q14"],
+                    choices=["heat_mode", "batch", "warmstart", "d3q14", "small"],
                     help="heat_mode: 8192^2 throughput (default); batch: 512 channels "
                          "solved to steady state; warmstart: learned warm start vs cold "
                          "start on 512 held-out channels; d3q14: 3-D D3Q14 throughput "
-                         "on a periodic nz x ny x nx lattice (--n3 cells per side)")
+                         "on a periodic nz x ny x nx lattice (--n3 cells per side); small: "
+                         "the 128x32 Poiseuille channel (FP64, FP32) and the 4096x4 "
+                         "second-sound pulse (FP32), time per step and error vs the oracle")
     ap.add_argument("--n3", type=int, default=512)
     ap.add_argument("--train-instances", type=int, default=4096)
     ap.add_argument("--train-steps", type=int, default=4000)
@@ -491,6 +493,61 @@ def run_d3q14(args):
     lat.close()
 
 
+def run_small(args):
+    """The two small named workloads: the 128x32 phonon Poiseuille channel
+    (10 000 steps, FP64 and FP32 storage) and the 4096x4 second-sound pulse
+    (5 000 steps, Kn_R = 0.1, 1, 10, FP32).  Both live in L2 and are bound by
+    launch latency, so the figure is the time per step of graph-captured
+    launches; each run is compared with the FP64 oracle (err_e, err_q as in
+    the parity tests)."""
+    import torch
+    import oracle
+    import paper_2010_01847_gb300 as plbm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    oracle.set_threads(os.cpu_count() or 1)
+    runs = []
+
+    def one(w, precision):
+        tau_N = plbm.tau_from_kn(w.kn_N, w.length)
+        tau_R = plbm.tau_from_kn(w.kn_R, w.length)
+        fields = inputs.initial_fields(w)
+        lat = plbm.Lattice(w.nx, w.ny, tau_N, tau_R, w.bc_x, w.bc_y, w.delta_e,
+                           precision=precision)
+        lat.init(*fields)
+        warm = 64                                      # warm-up; captures the step graphs
+        lat.step(warm)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        lat.step(w.steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        us = t0.elapsed_time(t1) * 1e3 / w.steps
+        g = lat.moments()
+        o = oracle.run(w.nx, w.ny, tau_N, tau_R, *fields, steps=warm + w.steps, bc_x=w.bc_x,
+                       bc_y=w.bc_y, delta_e=w.delta_e).moments()
+        de = np.abs(o[0] - o[0].mean()).max()
+        qmax = max(np.abs(o[1]).max(), np.abs(o[2]).max())
+        err_e = float(np.abs(g[0] - o[0]).max() / de)
+        err_q = float(max(np.abs(g[1] - o[1]).max(), np.abs(g[2] - o[2]).max()) / qmax)
+        runs.append({"workload": w.name, "storage": precision, "steps": w.steps,
+                     "us_per_step": us, "glups": w.nx * w.ny / us / 1e3, "kernel": lat.kernel,
+                     "err_e_vs_oracle": err_e, "err_q_vs_oracle": err_q})
+        lat.close()
+
+    one(inputs.POISEUILLE_128x32, "fp64")
+    one(inputs.POISEUILLE_128x32, "fp32")
+    for kn_R in (0.1, 1.0, 10.0):
+        one(inputs.second_sound_4096x4(kn_R), "fp32")
+    line = {"metric": "time per step, small named workloads (graph-captured)",
+            "value": runs[1]["us_per_step"], "unit": "us/step", "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "poiseuille_128x32 (value: FP32) + second_sound_4096x4"},
+            "runs": runs, "gpu_launches": sum(r["steps"] for r in runs) + 64 * len(runs)}
+    print(json.dumps(line), flush=True)
+
+
 def batch_instances(n, seed=inputs.SEED):
     """The batched-channel workload: seeded candidates (width W in [16, 512],
     length 4W, Kn_N log-U[1e-3, 1e-1], Kn_R log-U[0.1, 10], walls, periodic
@@ -644,6 +701,8 @@ def main():
         run_warmstart(args)
     elif args.workload == "d3q14":
         run_d3q14(args)
+    elif args.workload == "small":
+        run_small(args)
     else:
         run_native(args)
 
