@@ -352,11 +352,16 @@ class Lattice:
     def sync(self):
         self._check(self._lib.lbm_sync(self._ctx))
 
-    def moments(self):
-        """(e, qx, qy) of the current state as numpy [ny, nx] float64."""
-        e = np.empty((self.ny, self.nx))
-        qx = np.empty_like(e)
-        qy = np.empty_like(e)
+    def moments(self, out=None):
+        """(e, qx, qy) of the current state as numpy [ny, nx] float64.
+        ``out``: three C-contiguous float64 arrays of that shape to fill
+        (e.g. views of pinned host memory, so the copy runs at full speed)."""
+        if out is None:
+            out = [np.empty((self.ny, self.nx)) for _ in range(3)]
+        for a in out:
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != self.nx * self.ny:
+                raise ValueError("out arrays must be C-contiguous float64 of ny*nx elements")
+        e, qx, qy = out
         self._check(self._lib.lbm_moments(self._ctx, _dptr(e), _dptr(qx), _dptr(qy)))
         return e, qx, qy
 

@@ -73,17 +73,8 @@ __device__ __forceinline__ void item_sum5(const double (&v)[5], double *out) {
     __syncthreads();
 }
 
-// The plain step is latency-bound on its loads like the single-lattice
-// vector kernel, so for FP32 it is compiled per item size (MAXT threads per
-// block) for as many resident blocks per SM as 48 registers allow; the
-// residual modes and the other storage kinds keep the compiler's choice.
-template <typename T, int MAXT> struct BatchMinBlocks { static constexpr int value = 1; };
-template <> struct BatchMinBlocks<float, 128> { static constexpr int value = 10; };
-template <> struct BatchMinBlocks<float, 256> { static constexpr int value = 5; };
-template <> struct BatchMinBlocks<float, 512> { static constexpr int value = 2; };
-
-template <typename T, int MODE, int MAXT>
-__global__ void __launch_bounds__(MAXT, MODE == B_STEP ? BatchMinBlocks<T, MAXT>::value : 1)
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512)
 batch_kernel(const T *__restrict__ src, T *__restrict__ dst,
              const InstDev<typename Store<T>::C> *__restrict__ inst,
              const Item *__restrict__ items, const int *__restrict__ n_items,
@@ -411,23 +402,15 @@ cudaError_t launch_mode(lbm_batch *b, int mode, int src, cudaStream_t s) {
     const auto *tab = (const InstDev<C> *)b->dinst;
     const C inv_s = (C)(1.0 / b->scale);
     const int hp = b->have_prev ? 1 : 0;
-    if (mode == B_STEP) {
-        if (b->tpi == 128)
-            batch_kernel<T, B_STEP, 128><<<b->grid, b->tpi, 0, s>>>(
-                in, out, tab, b->ditems, b->dcounts, inv_s, (C *)b->hist, hp, b->partials);
-        else if (b->tpi == 256)
-            batch_kernel<T, B_STEP, 256><<<b->grid, b->tpi, 0, s>>>(
-                in, out, tab, b->ditems, b->dcounts, inv_s, (C *)b->hist, hp, b->partials);
-        else
-            batch_kernel<T, B_STEP, 512><<<b->grid, b->tpi, 0, s>>>(
-                in, out, tab, b->ditems, b->dcounts, inv_s, (C *)b->hist, hp, b->partials);
-    } else if (mode == B_STEP_RES) {
-        batch_kernel<T, B_STEP_RES, 512><<<b->grid, b->tpi, 0, s>>>(
+    if (mode == B_STEP)
+        batch_kernel<T, B_STEP><<<b->grid, b->tpi, 0, s>>>(in, out, tab, b->ditems, b->dcounts,
+                                                          inv_s, (C *)b->hist, hp, b->partials);
+    else if (mode == B_STEP_RES)
+        batch_kernel<T, B_STEP_RES><<<b->grid, b->tpi, 0, s>>>(
             in, out, tab, b->ditems, b->dcounts, inv_s, (C *)b->hist, hp, b->partials);
-    } else {
-        batch_kernel<T, B_RES_ONLY, 512><<<b->grid, b->tpi, 0, s>>>(
+    else
+        batch_kernel<T, B_RES_ONLY><<<b->grid, b->tpi, 0, s>>>(
             in, out, tab, b->ditems, b->dcounts, inv_s, (C *)b->hist, hp, b->partials);
-    }
     return cudaGetLastError();
 }
 
@@ -447,14 +430,7 @@ cudaError_t launch_finalize_batch(lbm_batch *b, cudaStream_t s) {
 
 template <typename T>
 cudaError_t occupancy(int tpi, int *per_sm) {
-    if (tpi == 128)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<T, B_STEP, 128>,
-                                                             tpi, 0);
-    if (tpi == 256)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<T, B_STEP, 256>,
-                                                             tpi, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<T, B_STEP, 512>,
-                                                         tpi, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<T, B_STEP>, tpi, 0);
 }
 
 cudaError_t plan_grid(lbm_batch *b) {
