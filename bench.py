@@ -342,8 +342,8 @@ def run_native(args):
                 events.append((a, b, plain))
             launches += plain
             if plain < k:
-                lat.step_residual(1)
-                launches += 2          # fused step + fixed-order finalize
+                lat.step_residual(1)   # fused step + fixed-order total
+                launches += 1
             done += k
         return launches
 
@@ -354,17 +354,19 @@ def run_native(args):
     torch.cuda.synchronize()
     events = []
     sampler = ClockSampler(dev.index)
+    launches0 = lat.kernel_launches
     with sampler:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        launches = chunked(args.steps, events)
+        chunked(args.steps, events)
         t1.record(stream)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     elapsed = t0.elapsed_time(t1) / 1e3
+    launches = lat.kernel_launches - launches0        # counted by the library
     kern_s = sum(a.elapsed_time(b) for a, b, _ in events) / 1e3
     kern_steps = sum(k for _, _, k in events)
     elapsed = max_over_ranks(elapsed, dist, dev)

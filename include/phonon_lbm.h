@@ -120,7 +120,9 @@ typedef enum {
 
 /* Which stream-collide kernel lbm_step launches. */
 typedef enum {
-    LBM_KERNEL_AUTO = 0,     /* fastest kernel valid for the lattice          */
+    LBM_KERNEL_AUTO = 0,     /* staged for 16-bit storage on >= 2^22 nodes,   */
+                             /* else vector when nx allows, else scalar       */
+                             /* (lbm_autotune times the candidates instead)   */
     LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx; the only kernel  */
                              /* for lattices with LBM_BC_SIDES                */
     LBM_KERNEL_VECTOR = 2,   /* 16-byte vectors along x; nx % (16/size) == 0  */

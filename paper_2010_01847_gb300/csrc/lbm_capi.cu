@@ -193,6 +193,8 @@ cudaError_t dispatch(const lbm_ctx *c, A... a) {
 }
 
 int *status_word(const lbm_ctx *c) { return (int *)(c->aux + 6); }
+// the middle level of the two-pass residual total, after the block partials
+double *mid_ptr(const lbm_ctx *c) { return c->partials + 5 * c->partial_blocks; }
 double *sums_ptr(const lbm_ctx *c) { return c->aux; }
 
 template <typename T> struct StepOp {
@@ -237,7 +239,7 @@ template <typename T> struct ResidualOp {
         using C = typename Store<T>::C;
         return launch_residual<T>((const T *)c->buf[1 - c->cur], make_readout(c),
                                   make_coef<C>(c), (C *)c->prev, c->have_prev, c->partials,
-                                  sums_ptr(c), c->stream);
+                                  sums_ptr(c), c->stream, mid_ptr(c));
     }
 };
 template <typename T> struct InitOp {
@@ -273,7 +275,8 @@ lbm_status ensure_scratch(lbm_ctx *c, bool need_prev) {
             cudaFree(c->partials);
             c->partials = nullptr;
             c->partial_blocks = 0;
-            CK(c, cudaMalloc(&c->partials, sizeof(double) * 5 * (size_t)blocks));
+            // + FINALIZE_MID records: the middle level of the two-pass total
+            CK(c, cudaMalloc(&c->partials, sizeof(double) * 5 * (size_t)(blocks + FINALIZE_MID)));
             c->partial_blocks = blocks;
         }
         if (!c->prev)
@@ -329,7 +332,13 @@ int resolve_kernel(lbm_ctx *c, int requested) {
         else (void)cudaGetLastError();
     }
     if (requested == KERNEL_AUTO) {
-        if (staged_ok) return KERNEL_STAGED;
+        // without timing (lbm_autotune times them): the staged kernel for
+        // 16-bit storage on large lattices (measured 5.7 against 4.7 TB/s at
+        // 8192^2), the vector kernel otherwise (6.7 against 5.7 TB/s for
+        // FP32; small lattices are launch-latency bound and take the kernel
+        // with the least set-up)
+        const bool sixteen = c->precision == PREC_FP16 || c->precision == PREC_BF16;
+        if (staged_ok && sixteen && c->plane >= (1LL << 22)) return KERNEL_STAGED;
         return vec_ok ? KERNEL_VECTOR : KERNEL_SCALAR;
     }
     if (requested == KERNEL_VECTOR && !vec_ok) return -1;
@@ -680,7 +689,9 @@ lbm_status lbm_step_residual(lbm_ctx *c, long n, double *r, double *total_energy
     c->cur = 1 - c->cur;
     c->n += 1;
     c->launches += 1;
-    CK(c, launch_finalize(c->partials, blocks, sums_ptr(c), c->stream));
+    int fin = 0;
+    CK(c, launch_finalize(c->partials, blocks, sums_ptr(c), c->stream, mid_ptr(c), &fin));
+    c->launches += fin;
     double sums[5];
     CK(c, cudaMemcpyAsync(sums, sums_ptr(c), sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));

@@ -73,8 +73,15 @@ cudaError_t launch_wait_probe(int *status, cudaStream_t stream);
 long long readout_blocks(int precision, int nx, int ny, int bc_x, int bc_y);
 
 // Fixed-order sum of per-block partials (5 doubles each) into sums[0..4].
+// With `mid` (room for FINALIZE_MID x 5 doubles) and more than
+// FINALIZE_SPLIT blocks it takes two launches: FINALIZE_MID blocks each sum
+// a contiguous run of partials in order, then one block sums their results
+// in order (still a fixed order: the result does not vary between runs).
+// Returns the number of launches in *launches when non-null.
+constexpr int FINALIZE_MID = 128;
+constexpr int FINALIZE_SPLIT = 8192;
 cudaError_t launch_finalize(const double *partials, int blocks, double *sums,
-                            cudaStream_t stream);
+                            cudaStream_t stream, double *mid = nullptr, int *launches = nullptr);
 
 // Read-out of the state at the current step.  `pulled` = the state is the
 // pull of the post-collision planes in `src` (step >= 1); otherwise `src`
@@ -104,7 +111,7 @@ constexpr int RESIDUAL_BLOCKS = 1216;    // 8 blocks per SM on 152 SMs
 template <typename T>
 cudaError_t launch_residual(const T *src, const Readout &r, const Coef<typename Store<T>::C> &k,
                             typename Store<T>::C *prev, bool have_prev, double *partials,
-                            double *sums, cudaStream_t stream);
+                            double *sums, cudaStream_t stream, double *mid = nullptr);
 
 // Initial state from device fields (Eq. 15): writes the state of step 0 into
 // `pre` and its collision into `post`.  qx/qy may be null.

@@ -153,14 +153,18 @@ __global__ void populations_kernel(const T *__restrict__ src, Readout r,
 // block of FINALIZE_THREADS; each thread sums every FINALIZE_THREADS-th
 // record, four records per iteration so that enough loads are in flight for
 // one SM to stream the ~2.6 MB of partials of an 8192^2 lattice.
+// Block k sums records [k chunk, min((k + 1) chunk, blocks)) into out[5 k ..].
 constexpr int FINALIZE_THREADS = 1024;
 
 __global__ void __launch_bounds__(FINALIZE_THREADS)
-finalize_sums(const double *__restrict__ partials, int blocks, double *__restrict__ sums) {
+finalize_sums(const double *__restrict__ partials, int blocks, int chunk,
+              double *__restrict__ out) {
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     const int stride = FINALIZE_THREADS;
-    int b = threadIdx.x;
-    for (; b + 3 * stride < blocks; b += 4 * stride) {
+    const int first = blockIdx.x * chunk;
+    const int end = min(blocks, first + chunk);
+    int b = first + threadIdx.x;
+    for (; b + 3 * stride < end; b += 4 * stride) {
         double v[4][5];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -171,11 +175,11 @@ finalize_sums(const double *__restrict__ partials, int blocks, double *__restric
 #pragma unroll
             for (int q = 0; q < 5; ++q) acc[q] += v[u][q];
     }
-    for (; b < blocks; b += stride) {
+    for (; b < end; b += stride) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) acc[q] += partials[(size_t)b * 5 + q];
     }
-    block_sum5_store(acc, sums);
+    block_sum5_store(acc, out + (size_t)blockIdx.x * 5);
 }
 
 // Eq. 15 on deviations, in the compute type: d_i = s (w_i (e - e_ref) +
@@ -283,7 +287,7 @@ cudaError_t launch_populations(const T *src, const Readout &r,
 template <typename T>
 cudaError_t launch_residual(const T *src, const Readout &r, const Coef<typename Store<T>::C> &k,
                             typename Store<T>::C *prev, bool have_prev, double *partials,
-                            double *sums, cudaStream_t stream) {
+                            double *sums, cudaStream_t stream, double *mid) {
     int blocks;
     if (vec_ok<T>(r)) {
         blocks = (int)vec_blocks<T>(r);
@@ -296,12 +300,23 @@ cudaError_t launch_residual(const T *src, const Readout &r, const Coef<typename 
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    return launch_finalize(partials, blocks, sums, stream);
+    return launch_finalize(partials, blocks, sums, stream, mid);
 }
 
 cudaError_t launch_finalize(const double *partials, int blocks, double *sums,
-                            cudaStream_t stream) {
-    finalize_sums<<<1, FINALIZE_THREADS, 0, stream>>>(partials, blocks, sums);
+                            cudaStream_t stream, double *mid, int *launches) {
+    if (mid && blocks > FINALIZE_SPLIT) {
+        const int chunk = (blocks + FINALIZE_MID - 1) / FINALIZE_MID;
+        const int parts = (blocks + chunk - 1) / chunk;
+        finalize_sums<<<parts, FINALIZE_THREADS, 0, stream>>>(partials, blocks, chunk, mid);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        finalize_sums<<<1, FINALIZE_THREADS, 0, stream>>>(mid, parts, parts, sums);
+        if (launches) *launches = 2;
+    } else {
+        finalize_sums<<<1, FINALIZE_THREADS, 0, stream>>>(partials, blocks, blocks, sums);
+        if (launches) *launches = 1;
+    }
     return cudaGetLastError();
 }
 
@@ -331,7 +346,7 @@ cudaError_t launch_max_deviation(const double *e, const double *qx, const double
                                                cudaStream_t);                                 \
     template cudaError_t launch_residual<T>(const T *, const Readout &,                       \
                                             const Coef<Store<T>::C> &, Store<T>::C *, bool,   \
-                                            double *, double *, cudaStream_t);                \
+                                            double *, double *, cudaStream_t, double *);      \
     template cudaError_t launch_init<T>(const double *, const double *, const double *, int,  \
                                         int, double, double, const Coef<Store<T>::C> &, T *,  \
                                         T *, cudaStream_t);

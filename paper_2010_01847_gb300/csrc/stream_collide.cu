@@ -53,9 +53,11 @@ step_scalar(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
 // Occupancy: the kernel is latency-bound on its loads, so it is compiled for
 // as many resident 256-thread blocks per SM as the register file allows
 // without heavy spilling (FP32: 5 blocks = 48 registers, 16 bytes spilled;
-// measured 6.73 TB/s at 8192^2 against 6.29 TB/s at 4 blocks / 54 registers).
+// measured 6.73 TB/s at 8192^2 against 6.29 TB/s at 4 blocks / 54 registers;
+// the residual step at 4 blocks = 64 registers costs 560 us over a plain step
+// against 680 us at 3 blocks, despite spilling 68 bytes).
 template <typename T> struct VecMinBlocks { static constexpr int plain = 3, res = 2; };
-template <> struct VecMinBlocks<float> { static constexpr int plain = 5, res = 3; };
+template <> struct VecMinBlocks<float> { static constexpr int plain = 5, res = 4; };
 template <> struct VecMinBlocks<double> { static constexpr int plain = 4, res = 3; };
 
 template <typename T, bool RES>
