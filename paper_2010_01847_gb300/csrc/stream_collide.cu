@@ -104,6 +104,32 @@ step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
 }
 
 // ---------------------------------------------------------------------------
+// Threads per block of a step launch: 256, or fewer (a multiple of 32) when
+// the lattice is small, so that the launch still spreads over every SM: a
+// small lattice is latency-bound, and FP64 arithmetic runs at about one
+// operation per clock per SM on this GPU (the 128 x 32 FP64 channel would
+// otherwise run on 8 of the 152 SMs).
+int step_block_size(long long threads) {
+    static int sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        dev = 0;
+    }
+    if (!sms[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            v <= 0) {
+            (void)cudaGetLastError();
+            v = 152;
+        }
+        sms[dev] = v;
+    }
+    const long long per_sm = (threads + sms[dev] - 1) / sms[dev];
+    if (per_sm >= 256) return 256;
+    return (int)(per_sm <= 32 ? 32 : (per_sm + 31) / 32 * 32);
+}
+
 template <typename T>
 cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc_x, int bc_y,
                         const Coef<typename Store<T>::C> &k, int *status,
@@ -118,22 +144,23 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
                                      stream);
     const ResidualReq<typename Store<T>::C> none{};
     const long long threads = kernel == KERNEL_VECTOR ? plane / Pack<T>::V : plane;
-    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    const int bs = step_block_size(threads);
+    const unsigned blocks = (unsigned)((threads + bs - 1) / bs);
     if (blocks_out) *blocks_out = (int)blocks;
     if (kernel == KERNEL_VECTOR) {
         if (rq)
-            step_vector<T, true><<<blocks, 256, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
-                                                             k, *rq);
+            step_vector<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
+                                                            k, *rq);
         else
-            step_vector<T, false><<<blocks, 256, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
-                                                              bc_y, k, none);
+            step_vector<T, false><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
+                                                             k, none);
     } else {
         if (rq)
-            step_scalar<T, true><<<blocks, 256, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
-                                                             k, *rq);
+            step_scalar<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
+                                                            k, *rq);
         else
-            step_scalar<T, false><<<blocks, 256, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
-                                                              bc_y, k, none);
+            step_scalar<T, false><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
+                                                             k, none);
     }
     return cudaGetLastError();
 }
@@ -143,7 +170,8 @@ long long step_blocks(int kernel, int precision, int nx, int ny, const StagedPla
     (void)plan;
     if (kernel == KERNEL_STAGED) kernel = KERNEL_VECTOR;    // residual steps run there
     const long long threads = kernel == KERNEL_VECTOR ? plane / vector_width(precision) : plane;
-    return (threads + 255) / 256;
+    const int bs = step_block_size(threads);
+    return (threads + bs - 1) / bs;
 }
 
 int vector_width(int precision) {
