@@ -147,6 +147,31 @@ def oracle_sample(w, seconds: float):
                       f"{dt:.1f} s, FP64, host '{model}'"}
 
 
+def oracle_rate(instances, seconds: float):
+    """FP64 oracle (all host cores) on a bounded sample of batched channels:
+    each instance from a cold start for as many steps as fit its share of
+    `seconds`; returns (GLUPS, cores, description)."""
+    import oracle
+    cores, model = cpu_info()
+    oracle.set_threads(cores)
+    updates, spent = 0.0, 0.0
+    for i in instances:
+        lat = oracle.run(i["nx"], i["ny"], i["tau_N"], i["tau_R"], np.ones((i["ny"], i["nx"])),
+                         bc_x=i["bc_x"], bc_y=i["bc_y"], delta_e=i["delta_e"])
+        t0 = time.perf_counter()
+        lat.step(1)
+        one = time.perf_counter() - t0
+        n = max(1, int(seconds / len(instances) / max(one, 1e-6)))
+        t0 = time.perf_counter()
+        lat.step(n)
+        spent += time.perf_counter() - t0
+        updates += n * i["nx"] * i["ny"]
+    widths = ", ".join(str(i["ny"]) for i in instances)
+    return updates / spent / 1e9, oracle.get_threads(), \
+        f"{len(instances)} channels (W = {widths}), {updates:.3g} site updates in {spent:.1f} s, " \
+        f"FP64, host '{model}'"
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -525,15 +550,19 @@ def run_small(args):
         torch.cuda.synchronize()
         us = t0.elapsed_time(t1) * 1e3 / w.steps
         g = lat.moments()
+        t_o = time.perf_counter()
         o = oracle.run(w.nx, w.ny, tau_N, tau_R, *fields, steps=warm + w.steps, bc_x=w.bc_x,
                        bc_y=w.bc_y, delta_e=w.delta_e).moments()
+        t_o = time.perf_counter() - t_o
         de = np.abs(o[0] - o[0].mean()).max()
         qmax = max(np.abs(o[1]).max(), np.abs(o[2]).max())
         err_e = float(np.abs(g[0] - o[0]).max() / de)
         err_q = float(max(np.abs(g[1] - o[1]).max(), np.abs(g[2] - o[2]).max()) / qmax)
         runs.append({"workload": w.name, "storage": precision, "steps": w.steps,
                      "us_per_step": us, "glups": w.nx * w.ny / us / 1e3, "kernel": lat.kernel,
-                     "err_e_vs_oracle": err_e, "err_q_vs_oracle": err_q})
+                     "err_e_vs_oracle": err_e, "err_q_vs_oracle": err_q,
+                     "oracle_us_per_step": t_o / (warm + w.steps) * 1e6,
+                     "oracle_threads": oracle.get_threads()})
         lat.close()
 
     one(inputs.POISEUILLE_128x32, "fp64")
@@ -612,7 +641,11 @@ def run_batch(args):
         t_seq += time.perf_counter() - t1
         seq_updates += n * i["nx"] * i["ny"]
         lat.close()
-    sample_batch_updates = float((steps[sample] * sites[sample]).sum())
+    cpu = None
+    if not args.no_cpu:
+        g_cpu, cores, desc = oracle_rate([inst[k] for k in sample[:4]], args.cpu_seconds)
+        cpu = {"value": g_cpu, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+               "sample": desc, "estimated_seconds_all": updates / (g_cpu * 1e9)}
     line = {
         "metric": "time to steady state (r < 1e-8), batched channels, cold start",
         "value": t_batch, "unit": "s", "n_gpus": 1, "higher_is_better": False,
@@ -629,6 +662,7 @@ def run_batch(args):
             "instances": len(sample), "seconds": t_seq, "site_updates": seq_updates,
             "glups": seq_updates / t_seq / 1e9,
             "estimated_seconds_all": t_seq * updates / max(seq_updates, 1.0)},
+        "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
 
