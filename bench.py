@@ -523,15 +523,31 @@ def run_small(args):
     (10 000 steps, FP64 and FP32 storage) and the 4096x4 second-sound pulse
     (5 000 steps, Kn_R = 0.1, 1, 10, FP32).  Both live in L2 and are bound by
     launch latency, so the figure is the time per step of graph-captured
-    launches; each run is compared with the FP64 oracle (err_e, err_q as in
-    the parity tests)."""
+    launches.  The CPU-baseline leg (skipped with --no-cpu) runs the FP64
+    oracle on the same inputs, on all host cores: its time per step, and the
+    GPU result's error against it (err_e, err_q as in the parity tests)."""
     import torch
-    import oracle
     import paper_2010_01847_gb300 as plbm
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    oracle.set_threads(os.cpu_count() or 1)
     runs = []
+
+    def cpu_leg(w, fields, tau_N, tau_R, steps, g):
+        import oracle
+        cores, model = cpu_info()
+        oracle.set_threads(cores)
+        t_o = time.perf_counter()
+        o = oracle.run(w.nx, w.ny, tau_N, tau_R, *fields, steps=steps, bc_x=w.bc_x,
+                       bc_y=w.bc_y, delta_e=w.delta_e).moments()
+        t_o = time.perf_counter() - t_o
+        de = np.abs(o[0] - o[0].mean()).max()
+        qmax = max(np.abs(o[1]).max(), np.abs(o[2]).max())
+        return {"kind": "oracle", "us_per_step": t_o / steps * 1e6,
+                "value": w.nx * w.ny * steps / t_o / 1e9, "unit": "GLUPS",
+                "cores": oracle.get_threads(), "sample": f"full run, FP64, host '{model}'",
+                "gpu_err_e": float(np.abs(g[0] - o[0]).max() / de),
+                "gpu_err_q": float(max(np.abs(g[1] - o[1]).max(),
+                                       np.abs(g[2] - o[2]).max()) / qmax)}
 
     def one(w, precision):
         tau_N = plbm.tau_from_kn(w.kn_N, w.length)
@@ -550,20 +566,12 @@ def run_small(args):
         torch.cuda.synchronize()
         us = t0.elapsed_time(t1) * 1e3 / w.steps
         g = lat.moments()
-        t_o = time.perf_counter()
-        o = oracle.run(w.nx, w.ny, tau_N, tau_R, *fields, steps=warm + w.steps, bc_x=w.bc_x,
-                       bc_y=w.bc_y, delta_e=w.delta_e).moments()
-        t_o = time.perf_counter() - t_o
-        de = np.abs(o[0] - o[0].mean()).max()
-        qmax = max(np.abs(o[1]).max(), np.abs(o[2]).max())
-        err_e = float(np.abs(g[0] - o[0]).max() / de)
-        err_q = float(max(np.abs(g[1] - o[1]).max(), np.abs(g[2] - o[2]).max()) / qmax)
-        runs.append({"workload": w.name, "storage": precision, "steps": w.steps,
-                     "us_per_step": us, "glups": w.nx * w.ny / us / 1e3, "kernel": lat.kernel,
-                     "err_e_vs_oracle": err_e, "err_q_vs_oracle": err_q,
-                     "oracle_us_per_step": t_o / (warm + w.steps) * 1e6,
-                     "oracle_threads": oracle.get_threads()})
+        lat_kernel = lat.kernel
         lat.close()
+        runs.append({"workload": w.name, "storage": precision, "steps": w.steps,
+                     "us_per_step": us, "glups": w.nx * w.ny / us / 1e3, "kernel": lat_kernel,
+                     "cpu_baseline": None if args.no_cpu else
+                     cpu_leg(w, fields, tau_N, tau_R, warm + w.steps, g)})
 
     one(inputs.POISEUILLE_128x32, "fp64")
     one(inputs.POISEUILLE_128x32, "fp32")
