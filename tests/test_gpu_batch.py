@@ -158,3 +158,44 @@ def test_batch_rejects_bad_instances():
     with pytest.raises(plbm.LBMError) as ex:
         plbm.Batch([MIXED[0], dict(nx=64, ny=4, tau_N=1.0, tau_R=1.0, bc_y=G)])
     assert ex.value.status == plbm.EUNSUPPORTED and "instance 1" in str(ex.value)
+
+
+def test_full_512_channel_batch_in_bench_configuration():
+    """The batched workload at its full size (512 seeded channels, 1.95e8
+    sites) in the bench's launch configuration (autotuned schedule), from the
+    cold start: the three smallest channels against the oracle element by
+    element, three others bit-identical to single-lattice runs."""
+    import bench
+    inst, _ = bench.batch_instances(512)
+    b = plbm.Batch(inst)
+    b.init()
+    b.autotune(4)
+    b.init()
+    steps = 24
+    b.step(steps)
+    sizes = np.array([i["nx"] * i["ny"] for i in inst])
+    small = np.argsort(sizes)[:3].tolist()
+    rng = np.random.default_rng(3)
+    other = rng.choice([k for k in range(len(inst)) if k not in small], 3, replace=False)
+    ones = lambda i: np.ones((i["ny"], i["nx"]))
+    for k in small:
+        i = inst[k]
+        o = oracle_run(i["nx"], i["ny"], i["tau_N"], i["tau_R"], (ones(i), None, None), steps,
+                       i["bc_x"], i["bc_y"], i["delta_e"])
+        eo, qxo, qyo = o.moments()
+        eg, qxg, qyg = b.moments(k)
+        # cold start: e - 1 and q start at zero, so scale by the oracle's range
+        err_e = np.abs(eg - eo).max() / max(np.abs(eo - 1.0).max(), 1e-30)
+        err_q = max(np.abs(qxg - qxo).max(), np.abs(qyg - qyo).max()) / \
+            max(np.abs(qxo).max(), np.abs(qyo).max())
+        assert err_e <= TOL["fp32"] and err_q <= TOL["fp32"], (k, err_e, err_q)
+    for k in other:
+        i = inst[int(k)]
+        lat = plbm.Lattice(i["nx"], i["ny"], i["tau_N"], i["tau_R"], i["bc_x"], i["bc_y"],
+                           i["delta_e"], kernel="vector")
+        lat.init(ones(i))
+        lat.step(steps)
+        for x, y in zip(b.moments(int(k)), lat.moments()):
+            assert np.array_equal(x, y), k
+        lat.close()
+    b.close()

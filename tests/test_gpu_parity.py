@@ -357,3 +357,34 @@ def test_device_init_matches_host_init():
     b.step(20)
     assert a.storage_scale == b.storage_scale
     assert np.array_equal(a.populations(), b.populations())
+
+
+# --- a lattice whose plane offsets pass 2^31 elements ------------------------
+def test_64bit_offsets_light_cone():
+    """20480 x 16384 FP32 (3.4e8 nodes, 21 GB of populations): the upper
+    planes start beyond 2^31 elements, so every index must be 64-bit.
+    Sampled nodes (the last ones included) after 12 steps against the oracle
+    on periodic light-cone windows."""
+    nx, ny, n = 20480, 16384, 12
+    assert 7 * nx * ny > 2 ** 31
+    tau_N, tau_R = 0.9, 15.0
+    e = inputs.sine_mode(nx, ny, 517.0, 1e-3, direction="xy")
+    g = gpu_run(nx, ny, tau_N, tau_R, (e, None, None), n)
+    assert g.kernel == "vector"
+    ge, gqx, gqy = g.moments_device()
+    rng = np.random.default_rng(4)
+    pts = [(ny - 1, nx - 1), (ny - 1, nx - 2), (ny - 2, 0), (0, 0), (0, nx - 1)] + \
+        [(int(a), int(b)) for a, b in zip(rng.integers(0, ny, 20), rng.integers(0, nx, 20))]
+    z = np.zeros((2 * n + 1, 2 * n + 1))
+    res = []
+    for (y, x) in pts:
+        o = oracle_run(2 * n + 1, 2 * n + 1, tau_N, tau_R, (_window(e, y, x, n), z, z), n)
+        oe, oqx, oqy = o.moments()
+        res.append((ge[y, x].item(), gqx[y, x].item(), gqy[y, x].item(),
+                    oe[n, n], oqx[n, n], oqy[n, n]))
+    del ge, gqx, gqy
+    g.close()
+    res = np.array(res)
+    err_e = np.abs(res[:, 0] - res[:, 3]).max() / np.abs(res[:, 3] - 1.0).max()
+    err_q = np.abs(res[:, 1:3] - res[:, 4:6]).max() / np.abs(res[:, 4:6]).max()
+    assert err_e <= TOL["fp32"] and err_q <= TOL["fp32"], (err_e, err_q)
