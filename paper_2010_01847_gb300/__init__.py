@@ -238,7 +238,7 @@ class Lattice:
 
     def __init__(self, nx, ny, tau_N, tau_R, bc_x=PERIODIC, bc_y=PERIODIC, delta_e=0.0,
                  precision="fp32", e_ref=1.0, kernel="auto", device=None,
-                 torch_buffers=True, graph_chunk=None, sides=None):
+                 torch_buffers=True, graph_chunk=None, sides=None, buffers=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the phonon LBM runs only on the GPU")
@@ -254,12 +254,17 @@ class Lattice:
         with torch.cuda.device(self.device):
             self.stream = torch.cuda.current_stream(self.device)
             sp = ctypes.c_void_p(self.stream.cuda_stream)
-            if torch_buffers:
+            if torch_buffers or buffers is not None:
                 nbytes = self._lib.lbm_population_bytes(grid, self.precision)
                 if nbytes == 0:
                     raise LBMError(EINVAL, "invalid grid or precision")
-                self._bufs = [torch.empty(nbytes, dtype=torch.uint8, device=self.device)
-                              for _ in range(2)]
+                if buffers is not None:
+                    # caller-owned CUDA tensors (e.g. views into a larger allocation)
+                    self._bufs = list(buffers)
+                    nbytes = min(b.numel() * b.element_size() for b in self._bufs)
+                else:
+                    self._bufs = [torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+                                  for _ in range(2)]
                 st = self._lib.lbm_create_ex(grid, float(tau_N), float(tau_R), bc,
                                              self.precision, float(e_ref), sp,
                                              ctypes.c_void_p(self._bufs[0].data_ptr()),
