@@ -123,10 +123,10 @@ typedef enum {
     LBM_KERNEL_AUTO = 0,     /* staged for 16-bit storage on >= 2^22 nodes,   */
                              /* else vector when nx allows, else scalar       */
                              /* (lbm_autotune times the candidates instead)   */
-    LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx; the only kernel  */
-                             /* for lattices with LBM_BC_SIDES                */
+    LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx                   */
     LBM_KERNEL_VECTOR = 2,   /* 16-byte vectors along x; nx % (16/size) == 0  */
     LBM_KERNEL_STAGED = 3    /* bulk asynchronous copies (TMA engine) of row  */
+                             /* (not for lattices with LBM_BC_SIDES)          */
                              /* segments into a shared-memory ring; needs nx  */
                              /* a multiple of the tile width (4096/size with  */
                              /* the default shape)                            */

@@ -317,9 +317,12 @@ lbm_status finish_residual(lbm_ctx *c, const double (&sums)[5], double *r,
 }
 
 int resolve_kernel(lbm_ctx *c, int requested) {
-    if (has_sides(c))       // only the scalar pull applies the per-side rules
-        return (requested == KERNEL_AUTO || requested == KERNEL_SCALAR) ? KERNEL_SCALAR : -1;
     const bool vec_ok = c->nx % vector_width(c->precision) == 0;
+    if (has_sides(c)) {     // the per-side rules: scalar and vector kernels only
+        if (requested == KERNEL_AUTO) return vec_ok ? KERNEL_VECTOR : KERNEL_SCALAR;
+        if (requested == KERNEL_SCALAR) return KERNEL_SCALAR;
+        return (requested == KERNEL_VECTOR && vec_ok) ? KERNEL_VECTOR : -1;
+    }
     // the staged kernel also needs its plan (launch attributes, occupancy)
     // worked out on this device, here, outside any stream capture
     const int cw = c->cw_req > 0 ? c->cw_req : 8;
@@ -867,8 +870,8 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
     struct Cand { int kernel, stages, cw; };
     Cand cands[8];
     int nc = 0;
-    const bool sides = has_sides(c);      // the per-side rules run on the scalar kernel only
-    if (!sides && c->nx % vector_width(c->precision) == 0) cands[nc++] = {KERNEL_VECTOR, 0, 0};
+    const bool sides = has_sides(c);      // the per-side rules: scalar and vector kernels
+    if (c->nx % vector_width(c->precision) == 0) cands[nc++] = {KERNEL_VECTOR, 0, 0};
     else cands[nc++] = {KERNEL_SCALAR, 0, 0};
     for (int cw : {8, 4})
         if (!sides && staged_supported(c->precision, c->nx, c->ny, cw))

@@ -60,7 +60,10 @@ template <typename T> struct VecMinBlocks { static constexpr int plain = 3, res 
 template <> struct VecMinBlocks<float> { static constexpr int plain = 5, res = 4; };
 template <> struct VecMinBlocks<double> { static constexpr int plain = 4, res = 3; };
 
-template <typename T, bool RES>
+// SIDES: the instantiation for lattices with a BC_SIDES direction (the
+// per-side treatments of Section 2.5 after the pull, as in pull_node); the
+// others never see the side logic.
+template <typename T, bool RES, bool SIDES = false>
 __global__ void __launch_bounds__(256, RES ? VecMinBlocks<T>::res : VecMinBlocks<T>::plain)
 step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
             long long plane, int bc_x, int bc_y, Coef<typename Store<T>::C> k,
@@ -69,9 +72,12 @@ step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
     constexpr int V = Pack<T>::V;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     C d[8][V];
-    const VecPos p = vector_pull<T>(src, nx, ny, plane, bc_x, bc_y, k, t, d);
+    const VecPos p = vector_pull<T, SIDES>(src, nx, ny, plane, bc_x, bc_y, k, t, d);
     const int y = p.y, x0 = p.x0;
-    const bool active = p.active, bottom = p.bottom, top = p.top;
+    // the wall rows of Eq. 58 (with SIDES, p.bottom/p.top also flag y sides)
+    const bool walls = !SIDES || bc_y == BC_WALLS;
+    const bool active = p.active, bottom = p.bottom && walls, top = p.top && walls;
+    const bool open_x = SIDES && bc_x == BC_SIDES, open_y = SIDES && bc_y == BC_SIDES;
 
     C loc[5] = {C(0), C(0), C(0), C(0), C(0)};
     if (active) {
@@ -83,6 +89,9 @@ step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
             for (int i = 0; i < 8; ++i) n[j][i] = d[i][j];
             if (bottom) wall_bottom(n[j], k);
             if (top) wall_top(n[j], k);
+            if (SIDES && (open_x || open_y))
+                apply_sides(n[j], k, open_x && x0 + j == 0, open_x && x0 + j == nx - 1,
+                            open_y && y == 0, open_y && y == ny - 1);
         }
         if (RES) residual_vec<C, V>(n, k, rq.inv_scale, rq.prev, plane, out, rq.have_prev != 0,
                                     loc);
@@ -147,7 +156,15 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
     const int bs = step_block_size(threads);
     const unsigned blocks = (unsigned)((threads + bs - 1) / bs);
     if (blocks_out) *blocks_out = (int)blocks;
-    if (kernel == KERNEL_VECTOR) {
+    const bool sides = bc_x == BC_SIDES || bc_y == BC_SIDES;
+    if (kernel == KERNEL_VECTOR && sides) {
+        if (rq)
+            step_vector<T, true, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                                  bc_y, k, *rq);
+        else
+            step_vector<T, false, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                                   bc_y, k, none);
+    } else if (kernel == KERNEL_VECTOR) {
         if (rq)
             step_vector<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
                                                             k, *rq);

@@ -138,7 +138,10 @@ struct VecPos {
 
 // Pulls the populations arriving at the thread's V nodes (Eq. 13 left-hand
 // side, seam jump); wall unknowns are left at 0 for the caller's Eq. 58.
-template <typename T>
+// With SIDES, directions created with BC_SIDES are not periodic either:
+// populations that would come from beyond a side are left at 0 for the
+// caller's apply_sides (bottom/top then also flag the rows of y sides).
+template <typename T, bool SIDES = false>
 __device__ __forceinline__ VecPos vector_pull(const T *__restrict__ src, int nx, int ny,
                                               long long plane, int bc_x, int bc_y,
                                               const Coef<typename Store<T>::C> &k, long long t,
@@ -152,9 +155,12 @@ __device__ __forceinline__ VecPos vector_pull(const T *__restrict__ src, int nx,
     const int xv = active ? int(t - (long long)y * tpr) : 0;
     const int x0 = xv * V;
     const int lane = threadIdx.x & 31;
-    const bool walls = bc_y == BC_WALLS;
+    const bool walls = bc_y == BC_WALLS || (SIDES && bc_y == BC_SIDES);
     const bool bottom = walls && y == 0;
     const bool top = walls && y == ny - 1;
+    const bool open_x = SIDES && bc_x == BC_SIDES;
+    const bool left_side = open_x && x0 == 0;          // no node beyond x = 0
+    const bool right_side = open_x && x0 + V == nx;    // none beyond x = nx - 1
 
     // every load is issued before any is used: the 16-byte vectors and, for
     // the lanes at a warp edge or a row end, the one neighbouring element of
@@ -178,8 +184,10 @@ __device__ __forceinline__ VecPos vector_pull(const T *__restrict__ src, int nx,
             for (int j = 0; j < V; ++j) d[i][j] = C(0);
         }
         edge[i] = C(0);
-        if (cx > 0 && need_left && !unknown) edge[i] = Store<T>::load(src[row + sx_left]);
-        if (cx < 0 && need_right && !unknown) edge[i] = Store<T>::load(src[row + sx_right]);
+        if (cx > 0 && need_left && !unknown && !left_side)
+            edge[i] = Store<T>::load(src[row + sx_left]);
+        if (cx < 0 && need_right && !unknown && !right_side)
+            edge[i] = Store<T>::load(src[row + sx_right]);
     }
 
 #pragma unroll

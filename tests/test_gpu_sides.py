@@ -44,11 +44,11 @@ def _oracle_sides(sides):
     return [s if s is not None else (oracle.DIFFUSE, 0.0) for s in sides]
 
 
-def _pair(case, precision, tau_N=0.9, tau_R=15.0, graph_chunk=None, seed=None):
+def _pair(case, precision, tau_N=0.9, tau_R=15.0, graph_chunk=None, seed=None, kernel="auto"):
     name, nx, ny, bcx, bcy, de, sides = case
     fields = inputs.random_state_fields(nx, ny, seed=seed or nx * 1000 + ny)
     g = plbm.Lattice(nx, ny, tau_N, tau_R, bcx, bcy, de, precision=precision,
-                     graph_chunk=graph_chunk,
+                     graph_chunk=graph_chunk, kernel=kernel,
                      sides={i: s for i, s in enumerate(sides) if s is not None})
     g.init(*fields)
     o = oracle.Lattice(nx, ny, tau_N, tau_R, bcx, bcy, de, _oracle_sides(sides))
@@ -64,11 +64,17 @@ def _compare(g, o, precision):
     return max(err_e, err_f), err_q
 
 
+VEC = {"fp32": 4, "fp64": 2, "fp16": 8, "bf16": 8}
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16", "bf16"])
+@pytest.mark.parametrize("kernel", ["scalar", "vector"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
-def test_sides_parity(case, precision):
-    g, o = _pair(case, precision)
-    assert g.kernel == "scalar"
+def test_sides_parity(case, kernel, precision):
+    if kernel == "vector" and case[1] % VEC[precision]:
+        pytest.skip(f"nx = {case[1]} is not a multiple of the vector width")
+    g, o = _pair(case, precision, kernel=kernel)
+    assert g.kernel == kernel
     for steps in (1, 57):
         g.step(steps - g.step_count)
         o.step(steps - o.step_count)
@@ -124,11 +130,39 @@ def test_sides_checkpoint_round_trip():
         np.testing.assert_array_equal(a, b)
 
 
+def test_sides_vector_equals_scalar_bitwise():
+    """The vector kernel's side treatment is the scalar kernel's, bit for bit
+    (same arithmetic in the same order), through a switched side."""
+    case = ("box", 96, 40, S, S, 0.0, [(ISO, 1.001), (ISO, 0.999), (FLX, 2e-4), (DIF, 0.0)])
+    fields = inputs.random_state_fields(96, 40, seed=5)
+    runs = []
+    for kernel in ("scalar", "vector"):
+        lat = plbm.Lattice(96, 40, 0.9, 15.0, S, S, 0.0, kernel=kernel, graph_chunk=8,
+                           sides={i: s for i, s in enumerate(case[6])})
+        lat.init(*fields)
+        lat.step(20)
+        lat.set_side(plbm.BOTTOM, DIF)
+        r, en = lat.step_residual(21)
+        runs.append((lat.populations(), lat.moments(), r, en))
+    (fa, ma, ra, ea), (fb, mb, rb, eb) = runs
+    assert np.array_equal(fa, fb)
+    for x, y in zip(ma, mb):
+        assert np.array_equal(x, y)
+    assert ea == pytest.approx(eb, rel=1e-12) and rb == pytest.approx(ra, rel=1e-6)
+
+
 def test_sides_kernel_choice_and_errors():
     lat = plbm.Lattice(64, 16, 0.9, 15.0, S, plbm.PERIODIC)
-    assert lat.kernel == "scalar"
+    assert lat.kernel == "vector"                    # nx a multiple of the vector width
     with pytest.raises(plbm.LBMError) as ei:
-        lat.set_kernel("vector")
+        lat.set_kernel("staged")
+    assert ei.value.status == plbm.EUNSUPPORTED
+    lat.set_kernel("scalar")
+    assert lat.kernel == "scalar"
+    ragged = plbm.Lattice(37, 16, 0.9, 15.0, S, plbm.PERIODIC)
+    assert ragged.kernel == "scalar"
+    with pytest.raises(plbm.LBMError) as ei:
+        ragged.set_kernel("vector")
     assert ei.value.status == plbm.EUNSUPPORTED
     with pytest.raises(plbm.LBMError) as ei:
         lat.set_side(plbm.BOTTOM, ISO, 1.0)          # y is periodic
@@ -141,7 +175,7 @@ def test_sides_kernel_choice_and_errors():
     assert ei.value.status == plbm.EINVAL
     lat.init(np.ones((16, 64)))
     lat.autotune(4)
-    assert lat.kernel == "scalar"
+    assert lat.kernel in ("scalar", "vector")
     # batches take periodic / gradient / walls only
     with pytest.raises(plbm.LBMError) as ei:
         plbm.Batch([dict(nx=64, ny=16, tau_N=0.9, tau_R=15.0, bc_x=S,
