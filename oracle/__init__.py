@@ -44,27 +44,42 @@ OMEGA = np.array([2 / 9] * 4 + [1 / 36] * 4)
 A_W = np.array([1 / 5] * 4 + [1 / 20] * 4)
 
 
+def compile_library(src: str, out: str) -> str:
+    """gcc the oracle source ``src`` into the shared library ``out``."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the C oracle into ``liboracle.so`` next to its source."""
     if not force and os.path.exists(_LIB) and \
             os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    return compile_library(_SRC, _LIB)
 
 
 _lib = None
+_lib_path = None          # another build of the oracle (see use_library)
+
+
+def use_library(path=None) -> None:
+    """Point the module at another build of the oracle source (the tests
+    that plant mistakes in the oracle use this); None returns to the
+    regular ``liboracle.so``."""
+    global _lib, _lib_path
+    _lib, _lib_path = None, path
 
 
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
+        if _lib_path is None:
+            build()
+        lib = ctypes.CDLL(_lib_path or _LIB)
         dp = ctypes.POINTER(ctypes.c_double)
         lib.orc_tau_from_kn.restype = ctypes.c_double
         lib.orc_tau_from_kn.argtypes = [ctypes.c_double, ctypes.c_double]
