@@ -107,3 +107,66 @@ def test_unmutated_copy_passes_the_same_pins(planted):
             if id(check) not in seen:
                 seen.add(id(check))
                 check()
+
+
+# --- the numpy oracles: D3Q14 / D1Q2 and the continuum solutions -----------------
+def test_lattice_pins_catch_wrong_d3q14_weights(monkeypatch):
+    """Corner flux weight 1/12 instead of 1/24: the moment conditions and the
+    continuum dispersion must reject it."""
+    import numpy as np
+    from oracle import lattices as lt
+    from tests import test_oracle_lattices as lat_pins
+    bad = lt.Lattice("D3Q14", 3, lt.D3Q14.c, lt.D3Q14.w,
+                     np.array([1 / 3] * 6 + [1 / 12] * 8), lt.D3Q14.speed)
+    monkeypatch.setattr(lat_pins, "D3", bad)
+    monkeypatch.setattr(lt, "D3Q14", bad)
+    with pytest.raises(AssertionError):
+        lat_pins.test_equilibrium_and_source_moments(bad)
+    with pytest.raises(AssertionError):
+        lat_pins.test_d3q14_longitudinal_modes_follow_eq52((1, 0, 0))
+
+
+def test_closed_form_pins_catch_planted_mistakes(monkeypatch):
+    import numpy as np
+    from oracle import analytic
+    from tests import test_oracle_sides as sp
+
+    good_1d = analytic.fourier_transient_1d
+
+    def film_without_third(X, t_star, kn_R, terms=4000):      # Kn^2 n^2 pi^2 t* (no /3)
+        return good_1d(X, 3.0 * t_star, kn_R, terms)
+    monkeypatch.setattr(analytic, "fourier_transient_1d", film_without_third)
+    with pytest.raises(AssertionError):
+        sp.test_fourier_transient_solves_heat_equation()
+    monkeypatch.setattr(analytic, "fourier_transient_1d", good_1d)
+
+    good_sq = analytic.square_steady
+
+    def square_flipped_qy(X, Y, Q0=1.0, terms=400):
+        th, qx, qy = good_sq(X, Y, Q0, terms)
+        return th, qx, -qy
+    monkeypatch.setattr(analytic, "square_steady", square_flipped_qy)
+    with pytest.raises(AssertionError):
+        sp.test_square_steady_solves_laplace_with_its_boundary_values()
+    monkeypatch.setattr(analytic, "square_steady", good_sq)
+
+    good_tr = analytic.heat_pulse_transforms
+
+    def pulse_wrong_reflection(X, kn_N, kn_R, t_pulse=100.0):  # C1 with the wrong sign
+        both = good_tr(X, kn_N, kn_R, t_pulse)
+        Xc = np.asarray(X, dtype=np.float64)[:, None]
+        kn_C = 1.0 / (1.0 / kn_N + 1.0 / kn_R)
+
+        def wrong(s):
+            Tb, Qb = both(s)
+            s = np.asarray(s, dtype=np.complex128)[None, :]
+            A = np.sqrt((kn_R / kn_N * s + 1.0) /
+                        (kn_N * kn_R / (3.0 * s) + 4.0 / 15.0 * kn_C * kn_R))
+            A = np.where(A.real < 0, -A, A)
+            C2 = (1.0 / s) * (1.0 - np.exp(-t_pulse * s)) / (1.0 - np.exp(-2.0 * A))
+            up = -C2 * np.exp(-A * (2.0 - Xc))
+            return Tb + 2 * (kn_N / s) * A * up, Qb - 2 * up
+        return wrong
+    monkeypatch.setattr(analytic, "heat_pulse_transforms", pulse_wrong_reflection)
+    with pytest.raises(AssertionError):
+        sp.test_heat_pulse_energy_balance_and_boundary_flux()

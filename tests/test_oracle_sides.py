@@ -109,6 +109,12 @@ def test_heat_pulse_energy_balance_and_boundary_flux():
     assert Q[0] == pytest.approx(1.0, abs=1e-4) and Q[1] == pytest.approx(0.0, abs=1e-4)
     _, Q = analytic.heat_pulse(np.array([0.0]), 150.0, kn_N, kn_R, gamma_t=9.0, terms=40000)
     assert Q[0] == pytest.approx(0.0, abs=2e-4)    # slow (1/terms) after the switch-off
+    # after the wave has reached the far side and been reflected (t* ~ 1340):
+    # still no flux through X = 1 and no energy lost
+    X = np.linspace(0, 1, 401)
+    th, Q = analytic.heat_pulse(X, 2500.0, kn_N, kn_R, gamma_t=9.0, terms=20000)
+    assert np.trapezoid(th, X) == pytest.approx(100 * kn_N, rel=1e-4)
+    assert abs(Q[-1]) < 1e-9
 
 
 # --- the side treatments of the oracle (Eqs. 55-58) ---------------------------
