@@ -114,3 +114,40 @@ def test_nd_errors_and_speed():
     g.init(np.ones(64))
     with pytest.raises(plbm.LBMError):
         g.init(np.full(64, np.nan))
+
+
+def test_d3q14_bench_configuration_light_cone():
+    """The D3Q14 bench workload at its full size (512^3, x-directed sine mode
+    plus seeded noise, FP32): sampled nodes after 12 steps against the oracle
+    on periodic (2n+1)^3 light-cone windows (a node after n steps depends only
+    on nodes within n cells)."""
+    n3, n = 512, 12
+    w = inputs.THROUGHPUT_8192
+    speed = plbm.LatticeND.lattice_speed(plbm.D3Q14)
+    tau_N, tau_R = w.kn_N * w.length * speed, w.kn_R * w.length * speed
+    x = np.arange(n3, dtype=np.float64)
+    e = np.empty((n3, n3, n3))
+    e[...] = 1.0 + 1e-3 * np.sin(2 * np.pi * x / 512.0)
+    e += inputs.uniform_noise(e.shape, 1e-6)
+    g = plbm.LatticeND(plbm.D3Q14, (n3, n3, n3), tau_N, tau_R)
+    g.init(e)
+    g.step(n)
+    ge, gq = g.moments()
+    g.close()
+    rng = np.random.default_rng(2)
+    pts = [(n3 - 1, n3 - 1, n3 - 1), (0, 0, 0)] + \
+        [tuple(int(v) for v in rng.integers(0, n3, 3)) for _ in range(10)]
+    res = []
+    for (z, y, xx) in pts:
+        idx = [np.arange(c - n, c + n + 1) % n3 for c in (z, y, xx)]
+        win = np.ascontiguousarray(e[np.ix_(*idx)])
+        o = lt.Run(lt.D3Q14, win.shape, tau_N, tau_R)
+        o.init(win)
+        o.step(n)
+        oe, oq = o.moments()
+        res.append((ge[z, y, xx] - oe[n, n, n], np.abs(gq[:, z, y, xx] - oq[:, n, n, n]).max(),
+                    abs(oe[n, n, n] - 1.0), np.abs(oq[:, n, n, n]).max()))
+    res = np.array(res)
+    err_e = np.abs(res[:, 0]).max() / res[:, 2].max()
+    err_q = res[:, 1].max() / res[:, 3].max()
+    assert err_e <= TOL["fp32"] and err_q <= TOL["fp32"], (err_e, err_q)
