@@ -315,7 +315,10 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  * 16-byte vectors) of all running instances, with each instance's own
  * coefficients (same scheme and boundaries as a single context).  The
  * steady-state solve replays a captured CUDA graph per check window and
- * retires converged instances on the device's work list. */
+ * retires converged instances on the device's work list.  Batching has no
+ * counterpart in the paper: each instance advances exactly by the scheme of
+ * Section 2 (Eq. 13 with Eqs. 15-16, 53-54, walls of Eq. 58, seam of
+ * Eqs. 59-60), bit-identical to a single context of the same instance. */
 typedef struct {
     int nx, ny;              /* nx a positive multiple of 16 / element size    */
     double tau_N, tau_R;     /* lattice steps, as lbm_create                   */
