@@ -110,7 +110,9 @@ typedef enum {
  * reference energy e_ref, with s = 1 for LBM_FP32 and a power of two chosen
  * at lbm_init for the 16-bit kinds (so the largest |d_i| sits near 2^12).
  * Collision arithmetic is FP32 for the FP32/FP16/BF16 kinds and FP64 for
- * LBM_FP64 (which also stores deviations, in double). */
+ * LBM_FP64 (which also stores deviations, in double).  The FP32 collision has
+ * a fixed operation order (each operation rounds once, no contraction left
+ * to the compiler), so every kernel kind gives the same bits. */
 typedef enum {
     LBM_FP32 = 0,
     LBM_FP16_DEV = 1,
@@ -120,8 +122,7 @@ typedef enum {
 
 /* Which stream-collide kernel lbm_step launches. */
 typedef enum {
-    LBM_KERNEL_AUTO = 0,     /* staged for 16-bit storage on >= 2^22 nodes,   */
-                             /* else vector when nx allows, else scalar       */
+    LBM_KERNEL_AUTO = 0,     /* vector when nx allows, else scalar            */
                              /* (lbm_autotune times the candidates instead)   */
     LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx                   */
     LBM_KERNEL_VECTOR = 2,   /* 16-byte vectors along x; nx % (16/size) == 0  */

@@ -335,13 +335,10 @@ int resolve_kernel(lbm_ctx *c, int requested) {
         else (void)cudaGetLastError();
     }
     if (requested == KERNEL_AUTO) {
-        // without timing (lbm_autotune times them): the staged kernel for
-        // 16-bit storage on large lattices (measured 5.7 against 4.7 TB/s at
-        // 8192^2), the vector kernel otherwise (6.7 against 5.7 TB/s for
-        // FP32; small lattices are launch-latency bound and take the kernel
-        // with the least set-up)
-        const bool sixteen = c->precision == PREC_FP16 || c->precision == PREC_BF16;
-        if (staged_ok && sixteen && c->plane >= (1LL << 22)) return KERNEL_STAGED;
+        // without timing (lbm_autotune times them): the vector kernel, the
+        // fastest measured at 8192^2 for every storage kind (FP32 6.7, 16-bit
+        // 6.5 TB/s against the staged kernel's 5.7 and 6.0), and with the
+        // least set-up for small, launch-latency bound lattices
         return vec_ok ? KERNEL_VECTOR : KERNEL_SCALAR;
     }
     if (requested == KERNEL_VECTOR && !vec_ok) return -1;

@@ -97,6 +97,83 @@ __device__ __forceinline__ void collide(C (&d)[8], const Coef<C> &k) {
     }
 }
 
+// FP32 arithmetic with its rounding spelled out: every operation rounds once,
+// in the order written, and the compiler chooses no contraction.  The same
+// sequence on float (one node) and on float2 (two nodes, packed FP32 pair
+// instructions, each lane rounded as the scalar operation) gives identical
+// bits, so every kernel that stores the collision in FP32 or 16 bits agrees
+// with every other to the bit whichever form it uses.
+__device__ __forceinline__ float f_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float f_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float f_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float f_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 f_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b rounded once: fma(b, -1, a) (the product is exact)
+__device__ __forceinline__ float2 f_sub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 f_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f_fma(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+}
+template <typename V> __device__ __forceinline__ V splat(float c);
+template <> __device__ __forceinline__ float splat<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 splat<float2>(float c) { return make_float2(c, c); }
+
+// One population's relaxation, d* = d - omega (d - eq) - sigma t_i, with
+// eq = w rho + t_i formed in one rounding (fused multiply-add) and t_i = +t
+// (plus) or -t (minus).  For minus the negated equilibrium -eq = w (-rho) + t
+// is formed instead (rounding is symmetric, so it is exactly -eq) and added.
+template <typename V>
+__device__ __forceinline__ V relax_plus(V d, V w, V rho, V t, V neg_omega, V neg_sigma) {
+    const V eq = f_fma(w, rho, t);
+    return f_fma(neg_sigma, t, f_fma(neg_omega, f_sub(d, eq), d));
+}
+template <typename V>
+__device__ __forceinline__ V relax_minus(V d, V w, V neg_rho, V t, V neg_omega, V sigma) {
+    const V neg_eq = f_fma(w, neg_rho, t);
+    return f_fma(sigma, t, f_fma(neg_omega, f_add(d, neg_eq), d));
+}
+
+// The collision above in FP32 on one node (V = float) or on two nodes at once
+// (V = float2: lane x one node, lane y the other).  Operation order chosen
+// for accuracy: over 5000 steps of the 4096 x 4 second-sound pulse
+// (Kn_R = 0.1) the max error against FP64 is 7e-6 with eq in one rounding,
+// 1.2e-5 with w rho rounded separately.
+template <typename V>
+__device__ __forceinline__ void collide_f32(V (&d)[8], const Coef<float> &k) {
+    const V rho = f_add(f_add(f_add(d[0], d[2]), f_add(d[1], d[3])),
+                        f_add(f_add(d[4], d[6]), f_add(d[5], d[7])));
+    const V s46 = f_sub(d[4], d[6]);
+    const V mx = f_add(f_add(f_sub(d[0], d[2]), s46), f_sub(d[7], d[5]));
+    const V my = f_add(f_add(f_sub(d[1], d[3]), s46), f_sub(d[5], d[7]));
+    const V neg_lambda = splat<V>(-k.lambda);
+    const V qx = f_fma(neg_lambda, mx, mx);             // q = m - lambda m
+    const V qy = f_fma(neg_lambda, my, my);
+    const V neg_rho = f_mul(splat<V>(-1.f), rho);       // exact
+    const V wa = splat<V>(k.w_axis), wd = splat<V>(k.w_diag);
+    const V ha = splat<V>(k.h_axis), hd = splat<V>(k.h_diag);
+    const V ta = f_mul(ha, qx);
+    const V tb = f_mul(ha, qy);
+    const V tp = f_mul(hd, f_add(qx, qy));
+    const V tm = f_mul(hd, f_sub(qx, qy));
+    const V no = splat<V>(-k.omega), ns = splat<V>(-k.sigma), sg = splat<V>(k.sigma);
+    // t_i for i = 0..7: ta, tb, -ta, -tb, tp, -tm, -tp, tm
+    d[0] = relax_plus(d[0], wa, rho, ta, no, ns);
+    d[1] = relax_plus(d[1], wa, rho, tb, no, ns);
+    d[2] = relax_minus(d[2], wa, neg_rho, ta, no, sg);
+    d[3] = relax_minus(d[3], wa, neg_rho, tb, no, sg);
+    d[4] = relax_plus(d[4], wd, rho, tp, no, ns);
+    d[5] = relax_minus(d[5], wd, neg_rho, tm, no, sg);
+    d[6] = relax_minus(d[6], wd, neg_rho, tp, no, sg);
+    d[7] = relax_plus(d[7], wd, rho, tm, no, ns);
+}
+
+// FP32 compute (FP32 and 16-bit storage): the spelled-out form.
+__device__ __forceinline__ void collide(float (&d)[8], const Coef<float> &k) {
+    collide_f32<float>(d, k);
+}
+
 // Eq. 58 on a wall node whose pulled incident populations are in d.
 // Bottom wall (y = 0, outward normal (0,-1)): unknown 1,4,5 from incident
 // 3,6,7; top wall (y = ny-1): unknown 3,6,7 from incident 1,4,5.  The sum of
@@ -114,6 +191,19 @@ __device__ __forceinline__ void wall_top(C (&d)[8], const Coef<C> &k) {
     d[3] = k.u_axis * s;
     d[6] = k.u_diag * s;
     d[7] = k.u_diag * s;
+}
+// The same on two nodes of one row at once (FP32 pairs; identical bits).
+__device__ __forceinline__ void wall_bottom(float2 (&d)[8], const Coef<float> &k) {
+    const float2 s = f_add(f_add(d[3], d[6]), d[7]);
+    d[1] = f_mul(splat<float2>(k.u_axis), s);
+    d[4] = f_mul(splat<float2>(k.u_diag), s);
+    d[5] = d[4];
+}
+__device__ __forceinline__ void wall_top(float2 (&d)[8], const Coef<float> &k) {
+    const float2 s = f_add(f_add(d[1], d[4]), d[5]);
+    d[3] = f_mul(splat<float2>(k.u_axis), s);
+    d[6] = f_mul(splat<float2>(k.u_diag), s);
+    d[7] = d[6];
 }
 
 // Section 2.5 on a node of the sides of BC_SIDES directions, after the

@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "lbm_kernels.h"
+#include "pairs16.cuh"
 
 namespace plbm {
 
@@ -129,48 +130,9 @@ template <> struct Vec16<double> {
                           (unsigned)__double2loint(o[1]), (unsigned)__double2hiint(o[1]));
     }
 };
-template <> struct Vec16<__half> {
-    static constexpr int V = 8;
-    __device__ static void unpack(uint4 r, float (&o)[8]) {
-        const unsigned w[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[j]));
-            o[2 * j] = f.x;
-            o[2 * j + 1] = f.y;
-        }
-    }
-    __device__ static uint4 pack(const float (&o)[8]) {
-        unsigned w[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const __half2 h = __floats2half2_rn(o[2 * j], o[2 * j + 1]);
-            w[j] = *reinterpret_cast<const unsigned *>(&h);
-        }
-        return make_uint4(w[0], w[1], w[2], w[3]);
-    }
-};
-template <> struct Vec16<__nv_bfloat16> {
-    static constexpr int V = 8;
-    __device__ static void unpack(uint4 r, float (&o)[8]) {
-        const unsigned w[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[j]));
-            o[2 * j] = f.x;
-            o[2 * j + 1] = f.y;
-        }
-    }
-    __device__ static uint4 pack(const float (&o)[8]) {
-        unsigned w[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
-            w[j] = *reinterpret_cast<const unsigned *>(&h);
-        }
-        return make_uint4(w[0], w[1], w[2], w[3]);
-    }
-};
+// 16-bit storage: the consumers keep the 16-byte vectors packed (pairs16.cuh)
+template <> struct Vec16<__half> { static constexpr int V = 8; };
+template <> struct Vec16<__nv_bfloat16> { static constexpr int V = 8; };
 
 template <typename T, int CW> constexpr int tile_width() { return CW * 32 * Vec16<T>::V; }
 template <typename T, int CW> constexpr int row_len() {
@@ -258,48 +220,70 @@ step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long
             const int y = (int)(tile / tiles_per_row);
             const int x0 = (int)(tile - (long long)y * tiles_per_row) * W;
             const T *stage = ring + (size_t)s * 8 * RL;
-            C d[8][V];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const T *r = stage + i * RL + V + t * V;
-                Vec16<T>::unpack(*reinterpret_cast<const uint4 *>(r), d[i]);
-                const int cx = cx_of(i);
-                if (cx > 0) {
-                    C left = Store<T>::load(r[-1]);
-                    if (bc_x == BC_GRADIENT && x0 == 0 && t == 0)
-                        left += (i < 4) ? k.jump_axis : k.jump_diag;     // Eq. 59
-#pragma unroll
-                    for (int j = V - 1; j >= 1; --j) d[i][j] = d[i][j - 1];
-                    d[i][0] = left;
-                } else if (cx < 0) {
-                    C right = Store<T>::load(r[V]);
-                    if (bc_x == BC_GRADIENT && x0 + W == nx && t == CW * 32 - 1)
-                        right -= (i < 4) ? k.jump_axis : k.jump_diag;    // Eq. 60
-#pragma unroll
-                    for (int j = 0; j < V - 1; ++j) d[i][j] = d[i][j + 1];
-                    d[i][V - 1] = right;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);     // this warp is done with the stage
-
             const bool bottom = walls && y == 0;
             const bool top = walls && y == ny - 1;
             const long long out = (long long)y * nx + x0 + t * V;
+            if constexpr (sizeof(T) == 2) {
+                // 16-bit storage: shift the packed words, collide node pairs
+                // (pairs16.cuh)
+                uint4 w[8];
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-                C n[8];
+                for (int i = 0; i < 8; ++i) {
+                    const T *r = stage + i * RL + V + t * V;
+                    const unsigned short *r16 = reinterpret_cast<const unsigned short *>(r);
+                    w[i] = *reinterpret_cast<const uint4 *>(r);
+                    const int cx = cx_of(i);
+                    if (cx > 0) w[i] = shift_from_left(w[i], (unsigned)r16[-1] << 16);
+                    else if (cx < 0) w[i] = shift_from_right(w[i], (unsigned)r16[V]);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);     // this warp is done with the stage
+                const bool grad = bc_x == BC_GRADIENT;
+                const bool jl = grad && x0 == 0 && t == 0;                  // Eq. 59
+                const bool jr = grad && x0 + W == nx && t == CW * 32 - 1;   // Eq. 60
+                collide_words16<T>(w, k, SeamAdd{jl, jl, jr, jr}, bottom, top);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) n[i] = d[i][j];
-                if (bottom) wall_bottom(n, k);
-                if (top) wall_top(n, k);
-                collide(n, k);
+                for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, w[i]);
+            } else {
+                C d[8][V];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) d[i][j] = n[i];
+                for (int i = 0; i < 8; ++i) {
+                    const T *r = stage + i * RL + V + t * V;
+                    Vec16<T>::unpack(*reinterpret_cast<const uint4 *>(r), d[i]);
+                    const int cx = cx_of(i);
+                    if (cx > 0) {
+                        C left = Store<T>::load(r[-1]);
+                        if (bc_x == BC_GRADIENT && x0 == 0 && t == 0)
+                            left += (i < 4) ? k.jump_axis : k.jump_diag;     // Eq. 59
+#pragma unroll
+                        for (int j = V - 1; j >= 1; --j) d[i][j] = d[i][j - 1];
+                        d[i][0] = left;
+                    } else if (cx < 0) {
+                        C right = Store<T>::load(r[V]);
+                        if (bc_x == BC_GRADIENT && x0 + W == nx && t == CW * 32 - 1)
+                            right -= (i < 4) ? k.jump_axis : k.jump_diag;    // Eq. 60
+#pragma unroll
+                        for (int j = 0; j < V - 1; ++j) d[i][j] = d[i][j + 1];
+                        d[i][V - 1] = right;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);     // this warp is done with the stage
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    C n[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) n[i] = d[i][j];
+                    if (bottom) wall_bottom(n, k);
+                    if (top) wall_top(n, k);
+                    collide(n, k);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) d[i][j] = n[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    st_stream(dst + (long long)i * plane + out, Vec16<T>::pack(d[i]));
             }
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                st_stream(dst + (long long)i * plane + out, Vec16<T>::pack(d[i]));
         }
     }
 }

@@ -9,6 +9,7 @@
 // With RES the kernel also accumulates the residual sums of the pulled state
 // (the state at step n) and writes one set of 5 partial sums per block.
 #include "lbm_kernels.h"
+#include "pairs16.cuh"
 #include "vector_pull.cuh"
 
 namespace plbm {
@@ -113,6 +114,86 @@ step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
 }
 
 // ---------------------------------------------------------------------------
+// Vector kernel for 16-bit storage, plain steps on periodic / gradient /
+// wall lattices: the step of step_vector with the node pairs of
+// pairs16.cuh.  The x shift runs on the packed words (the neighbour's word
+// from the adjacent lane, or at a warp edge or a row end the one element
+// loaded directly); the collision runs two nodes per packed FP32 pair
+// instruction, half the instructions of the node-by-node form, with the
+// same bits.  Inputs stay packed until their pair is needed, so the kernel
+// fits 4 blocks of 256 threads per SM (the node-by-node form: 3).
+namespace {
+
+__device__ __forceinline__ unsigned ld_u16(const void *p) {
+    unsigned short r;
+    asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(r) : "l"(p));
+    return r;
+}
+
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(256, 4)
+step_vector16(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long long plane,
+              int bc_x, int bc_y, Coef<float> k) {
+    static_assert(sizeof(T) == 2 && Pack<T>::V == 8, "16-bit storage");
+    constexpr int V = 8;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int tpr = nx / V;
+    const long long total = (long long)tpr * ny;
+    const bool active = t < total;
+    const int y = active ? int(t / tpr) : 0;
+    const int xv = active ? int(t - (long long)y * tpr) : 0;
+    const int x0 = xv * V;
+    const int lane = threadIdx.x & 31;
+    const bool walls = bc_y == BC_WALLS;
+    const bool bottom = walls && y == 0;
+    const bool top = walls && y == ny - 1;
+    const bool need_left = (lane == 0 || xv == 0) && active;
+    const bool need_right = (lane == 31 || xv + 1 == tpr) && active;
+    const int sx_left = x0 == 0 ? nx - 1 : x0 - 1;
+    const int sx_right = x0 + V >= nx ? x0 + V - nx : x0 + V;
+
+    // every load first (the vectors and the edge elements), as in vector_pull
+    uint4 w[8];
+    unsigned edge[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i);
+        int sy = y - cy;
+        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+        const long long row = (long long)i * plane + (long long)sy * nx;
+        const bool unknown = (cy > 0 && bottom) || (cy < 0 && top);
+        w[i] = (active && !unknown) ? ld_stream(src + row + x0) : make_uint4(0u, 0u, 0u, 0u);
+        edge[i] = 0u;
+        if (cx > 0 && need_left && !unknown) edge[i] = ld_u16(src + row + sx_left);
+        if (cx < 0 && need_right && !unknown) edge[i] = ld_u16(src + row + sx_right);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int cx = cx_of(i);
+        if (cx > 0) {
+            unsigned nb = __shfl_up_sync(0xffffffffu, w[i].w, 1);
+            if (need_left) nb = edge[i] << 16;
+            w[i] = shift_from_left(w[i], nb);
+        } else if (cx < 0) {
+            unsigned nb = __shfl_down_sync(0xffffffffu, w[i].x, 1);
+            if (need_right) nb = edge[i];
+            w[i] = shift_from_right(w[i], nb);
+        }
+    }
+    if (!active) return;
+    // at a warp edge or a row end the neighbour was loaded: the seam jump
+    // (zero away from the seam) is added there, as vector_pull does
+    const bool grad = bc_x == BC_GRADIENT;
+    const SeamAdd seam{need_left, x0 == 0 && grad, need_right, x0 + V == nx && grad};
+    collide_words16<T>(w, k, seam, bottom, top);
+    const long long out = (long long)y * nx + x0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, w[i]);
+}
+
+// ---------------------------------------------------------------------------
 // Threads per block of a step launch: 256, or fewer (a multiple of 32) when
 // the lattice is small, so that the launch still spreads over every SM: a
 // small lattice is latency-bound, and FP64 arithmetic runs at about one
@@ -165,12 +246,17 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
             step_vector<T, false, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
                                                                    bc_y, k, none);
     } else if (kernel == KERNEL_VECTOR) {
-        if (rq)
+        if (rq) {
             step_vector<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
                                                             k, *rq);
-        else
-            step_vector<T, false><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
-                                                             k, none);
+        } else {
+            if constexpr (sizeof(T) == 2)
+                step_vector16<T><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
+                                                            k);
+            else
+                step_vector<T, false><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                                 bc_y, k, none);
+        }
     } else {
         if (rq)
             step_scalar<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,

@@ -106,7 +106,7 @@ def test_parity_degenerate_relaxation(tau_N, tau_R):
     assert err_e <= TOL["fp32"] and err_q <= TOL["fp32"], (err_e, err_q)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16", "fp64"])
 @pytest.mark.parametrize("shape", [(2, 0, 4, 0), (3, 1, 8, 1), (6, 0, 4, 1), (2, 2, 8, 0)])
 def test_staged_shapes_agree_bitwise(precision, shape):
     """Every staged launch shape (ring depth, CTAs/SM, consumer warps, L2
@@ -145,7 +145,7 @@ def test_autotune_keeps_state_and_results(precision):
     assert np.array_equal(ref.populations(), fresh.populations())
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
 def test_kernels_and_graph_chunks_agree_bitwise(precision):
     nx, ny = 2048, 40
     fields = inputs.random_state_fields(nx, ny, seed=5)
