@@ -122,15 +122,25 @@ typedef enum {
 
 /* Which stream-collide kernel lbm_step launches. */
 typedef enum {
-    LBM_KERNEL_AUTO = 0,     /* vector when nx allows, else scalar            */
-                             /* (lbm_autotune times the candidates instead)   */
+    LBM_KERNEL_AUTO = 0,     /* resident for LBM_FP32 lattices of up to       */
+                             /* 16384 nodes, else vector when nx allows, else */
+                             /* scalar (lbm_autotune times the candidates)    */
     LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx                   */
     LBM_KERNEL_VECTOR = 2,   /* 16-byte vectors along x; nx % (16/size) == 0  */
-    LBM_KERNEL_STAGED = 3    /* bulk asynchronous copies (TMA engine) of row  */
+    LBM_KERNEL_STAGED = 3,   /* bulk asynchronous copies (TMA engine) of row  */
                              /* (not for lattices with LBM_BC_SIDES)          */
                              /* segments into a shared-memory ring; needs nx  */
                              /* a multiple of the tile width (4096/size with  */
                              /* the default shape)                            */
+    LBM_KERNEL_RESIDENT = 4  /* LBM_FP32 lattices small enough that both      */
+                             /* population buffers fit in the shared memory   */
+                             /* of one thread-block cluster (up to 16 CTAs,   */
+                             /* ~3.6 MB: 201 x 201 fits): lbm_step(n) is one  */
+                             /* launch of n steps, slabs exchanged through    */
+                             /* distributed shared memory; same results bit   */
+                             /* for bit.  lbm_set_kernel returns              */
+                             /* LBM_EUNSUPPORTED when the lattice does not    */
+                             /* fit or no cluster can be resident             */
 } lbm_kernel;
 
 typedef struct {

@@ -25,12 +25,12 @@ PERIODIC, PERIODIC_GRADIENT, DIFFUSE_WALLS, SIDES = 0, 1, 2, 3
 LEFT, RIGHT, BOTTOM, TOP = 0, 1, 2, 3                 # sides (lbm_side)
 DIFFUSE, ISOTHERMAL, HEAT_FLUX = 0, 1, 2              # side treatments (lbm_side_kind)
 FP32, FP16_DEV, BF16_DEV, FP64 = 0, 1, 2, 3
-KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_STAGED = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_STAGED, KERNEL_RESIDENT = 0, 1, 2, 3, 4
 
 D1Q2, D3Q14 = 1, 3                                     # lbm_lattice
 PRECISIONS = {"fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV, "fp64": FP64}
 KERNELS = {"auto": KERNEL_AUTO, "scalar": KERNEL_SCALAR, "vector": KERNEL_VECTOR,
-           "staged": KERNEL_STAGED}
+           "staged": KERNEL_STAGED, "resident": KERNEL_RESIDENT}
 _ELEM = {FP32: 4, FP16_DEV: 2, BF16_DEV: 2, FP64: 8}
 
 # Every symbol include/phonon_lbm.h declares.

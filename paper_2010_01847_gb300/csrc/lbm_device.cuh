@@ -256,15 +256,15 @@ __device__ __forceinline__ void apply_sides(C (&d)[8], const Coef<C> &k, bool on
 }
 
 // Generic pull of the 8 populations arriving at node (x, y) at the next
-// step from the post-collision planes `src` (one node, any nx).  Applies the
-// seam jump, the walls and the per-side treatments.  Used by the scalar step
-// kernel and by every read-out kernel.
-template <typename T>
-__device__ __forceinline__ void pull_node(const T *__restrict__ src, long long plane,
-                                          int nx, int ny, int x, int y, int bc_x,
-                                          int bc_y, const Coef<typename Store<T>::C> &k,
-                                          typename Store<T>::C (&d)[8]) {
-    using C = typename Store<T>::C;
+// step from post-collision planes (one node, any nx).  Applies the seam
+// jump, the walls and the per-side treatments.  `load(i, sx, sy)` returns
+// population i of node (sx, sy) in the compute type: pull_node reads global
+// planes (the scalar step kernel and every read-out kernel), the cluster-
+// resident kernel reads shared memory.
+template <typename C, typename Load>
+__device__ __forceinline__ void pull_node_with(const Load &load, int nx, int ny, int x, int y,
+                                               int bc_x, int bc_y, const Coef<C> &k,
+                                               C (&d)[8]) {
     const bool walls = bc_y == BC_WALLS;
     const bool sides_x = bc_x == BC_SIDES, sides_y = bc_y == BC_SIDES;
     const bool open_y = walls || sides_y;
@@ -290,7 +290,7 @@ __device__ __forceinline__ void pull_node(const T *__restrict__ src, long long p
             sx -= nx;
             if (bc_x == BC_GRADIENT) jump = -((i < 4) ? k.jump_axis : k.jump_diag);
         }
-        d[i] = Store<T>::load(src[(long long)i * plane + (long long)sy * nx + sx]) + jump;
+        d[i] = load(i, sx, sy) + jump;
     }
     if (walls) {
         if (y == 0) wall_bottom(d, k);
@@ -299,6 +299,18 @@ __device__ __forceinline__ void pull_node(const T *__restrict__ src, long long p
     if (sides_x || sides_y)
         apply_sides(d, k, sides_x && x == 0, sides_x && x == nx - 1, sides_y && y == 0,
                     sides_y && y == ny - 1);
+}
+
+template <typename T>
+__device__ __forceinline__ void pull_node(const T *__restrict__ src, long long plane,
+                                          int nx, int ny, int x, int y, int bc_x,
+                                          int bc_y, const Coef<typename Store<T>::C> &k,
+                                          typename Store<T>::C (&d)[8]) {
+    pull_node_with(
+        [&](int i, int sx, int sy) {
+            return Store<T>::load(src[(long long)i * plane + (long long)sy * nx + sx]);
+        },
+        nx, ny, x, y, bc_x, bc_y, k, d);
 }
 
 // Residual contribution of one node of the state at step n (pulled, after

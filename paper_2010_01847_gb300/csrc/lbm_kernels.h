@@ -18,7 +18,8 @@ struct NvtxRange {
 };
 
 enum { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2, PREC_FP64 = 3 };
-enum { KERNEL_AUTO = 0, KERNEL_SCALAR = 1, KERNEL_VECTOR = 2, KERNEL_STAGED = 3 };
+enum { KERNEL_AUTO = 0, KERNEL_SCALAR = 1, KERNEL_VECTOR = 2, KERNEL_STAGED = 3,
+       KERNEL_RESIDENT = 4 };
 
 // Sets the text lbm_last_error(NULL) returns.
 void set_global_error(const char *msg);
@@ -64,6 +65,34 @@ cudaError_t launch_step_staged(const T *src, T *dst, int nx, int ny, int bc_x, i
                                const Coef<typename Store<T>::C> &k, int *status,
                                const StagedPlan &plan, int *blocks_out, cudaStream_t stream);
 bool staged_supported(int precision, int nx, int ny, int consumer_warps);
+
+// Launch shape of the cluster-resident kernel (resident.cu): one cluster of
+// `cluster` CTAs, CTA r owning slab r of w columns (part_x) or rows.
+struct ResidentPlan {
+    int cluster = 0;    // CTAs in the one cluster (0: no plan)
+    int part_x = 0;     // 1: slabs of columns, 0: slabs of rows
+    int w = 0;          // columns (rows) per slab
+    int rows = 0;       // allocated rows of a slab plane (ghost rows included)
+    int cols = 0;       // allocated columns (ghost columns included)
+    int last_rank = 0;  // the last CTA with nodes
+    int npt = 0;        // nodes per thread (1..4)
+    int threads = 0;    // threads per CTA
+    int smem = 0;       // dynamic shared memory per CTA (bytes)
+};
+
+// A plan for an FP32 lattice whose two post-collision buffers fit in the
+// shared memory of one cluster (cluster_req > 0 asks for that many CTAs);
+// cudaErrorNotSupported when none fits or none can be resident on this
+// device.  Sets the kernel's launch attributes: call outside stream capture.
+cudaError_t resident_plan(int precision, int nx, int ny, int cluster_req, ResidentPlan *out);
+
+// `steps` (>= 1) time steps from the post-collision planes `src`: writes the
+// post-collision planes of the last step to out_last and of the step before
+// it to out_prev (src may be either; each CTA reads its own nodes before it
+// writes them).
+cudaError_t launch_resident(const float *src, float *out_last, float *out_prev, int nx, int ny,
+                            int bc_x, int bc_y, const Coef<float> &k, long steps,
+                            const ResidentPlan &p, cudaStream_t stream);
 
 // Runs the staged kernel's bounded mbarrier wait against a barrier nothing
 // completes (one CTA, ~2 s); the wait gives up and ORs 1 into *status.

@@ -1,0 +1,342 @@
+// Cluster-resident stream-collide for small lattices: many time steps in
+// one launch, the whole state in the shared memory of one thread-block
+// cluster.
+//
+// A lattice of a few thousand to a few tens of thousands of nodes (the
+// paper's own test lattices, 3 x 301 to 201 x 201; the 128 x 32 channel; the
+// 4096 x 4 second-sound line) does too little work per step to fill the GPU:
+// one launch per step costs more than the step.  Here one cluster of up to
+// 16 CTAs holds both post-collision buffers (8 planes each) in shared
+// memory.  CTA r owns a slab of the lattice (columns [r w, (r + 1) w) when
+// nx >= ny, else rows); each step every CTA pulls its nodes from the
+// current buffer -- its own slab from its shared memory, the neighbours'
+// edge nodes from theirs through distributed shared memory
+// (ld.shared::cluster) -- applies the seam jump, walls and sides, collides
+// (the same pull_node_with / collide as every other kernel: identical bits)
+// and writes the other buffer in its own shared memory; one cluster barrier
+// per step orders the writes of step n before the reads of step n + 1.
+// Global memory is read once at the start and written once at the end:
+// post-collision state of the last step and of the one before it, as
+// step-by-step launches would leave them (the read-outs pull from the
+// latter).
+//
+// The barrier is the hardware cluster barrier; every thread of every CTA
+// reaches it once per step (uniform loop bounds, no early exit), so no wait
+// depends on data.
+#include <algorithm>
+
+#include "lbm_kernels.h"
+
+namespace plbm {
+namespace {
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile(
+        "barrier.cluster.arrive.release.aligned;\n\t"
+        "barrier.cluster.wait.acquire.aligned;" ::
+            : "memory");
+}
+
+__device__ __forceinline__ float ld_cluster(uint32_t local_addr, unsigned rank) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote));
+    return v;
+}
+
+__device__ __forceinline__ void st_cluster(uint32_t local_addr, unsigned rank, float v) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(v) : "memory");
+}
+
+// Slab geometry shared by every CTA of the cluster.  A slab is stored with
+// one ghost column (part_x) or ghost row on each side: population i of local
+// node (lx, ly), lx in [-1, wx] and ly in [0, ny) for column slabs, sits at
+// ((buf 8 + i) rows + ly + gy) cols + lx + gx.
+struct Slabs {
+    int nx, ny;
+    int part_x;     // 1: slabs of columns, 0: slabs of rows
+    int w;          // columns (rows) per slab; the last slabs may hold fewer or none
+    int rows, cols; // allocated rows and columns of a slab plane (ghosts included)
+    int nr;         // CTAs in the cluster
+    int last_rank;  // the last CTA with nodes
+};
+
+template <int NPT>
+__global__ void __launch_bounds__(1024, 1)
+step_resident(const float *src, float *out_last, float *out_prev, long long plane, Slabs g,
+              int bc_x, int bc_y, Coef<float> k, long steps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *sm = reinterpret_cast<float *>(smem_raw);
+    const int rank = (int)cluster_rank();
+    const int nx = g.nx, ny = g.ny;
+    const bool px = g.part_x != 0;
+    const bool ghosts = g.nr > 1;
+    // this CTA's slab: [x0, x0 + wx) x [y0, y0 + wy)
+    const int x0 = px ? rank * g.w : 0;
+    const int y0 = px ? 0 : rank * g.w;
+    const int wx = px ? max(0, min(g.w, nx - x0)) : nx;
+    const int wy = px ? ny : max(0, min(g.w, ny - y0));
+    const int count = wx * wy;
+    const int gx = px ? 1 : 0, gy = px ? 0 : 1;
+    // 32-bit offsets: a CTA's shared memory holds fewer than 2^16 floats
+    auto at = [&](int buf, int i, int lx, int ly) -> float * {
+        return sm + (((buf * 8 + i) * g.rows + (ly + gy)) * g.cols + (lx + gx));
+    };
+    // this thread's nodes (fixed for the whole launch)
+    int nlx[NPT], nly[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int l = threadIdx.x + j * blockDim.x;
+        nly[j] = l < count ? l / wx : -1;        // -1: no node
+        nlx[j] = l < count ? l - nly[j] * wx : 0;
+    }
+
+    // Fills buffer b's ghosts from the neighbouring slabs (distributed shared
+    // memory): for column slabs, column x0 - 1 for the populations that
+    // move right (c_x = +1) and column x0 + wx for those that move left; for
+    // row slabs, the rows below and above for c_y = +1 / -1.  Periodic wrap
+    // across the lattice edge; a side or wall there is never pulled from.
+    auto fill_ghosts = [&](int b) {
+        if (!ghosts || count == 0) return;
+        const int across = px ? ny : nx;
+        const int lo_owner = px ? (x0 == 0 ? g.last_rank : rank - 1)
+                                : (y0 == 0 ? g.last_rank : rank - 1);
+        const int lo_src = px ? (x0 == 0 ? nx - 1 : x0 - 1) : (y0 == 0 ? ny - 1 : y0 - 1);
+        const int hi_edge = px ? x0 + wx : y0 + wy;
+        const int hi_owner = hi_edge == (px ? nx : ny) ? 0 : rank + 1;
+        const int hi_src = hi_edge == (px ? nx : ny) ? 0 : hi_edge;
+        for (int t = threadIdx.x; t < 6 * across; t += blockDim.x) {
+            const int side = t / (3 * across);            // 0: low ghost, 1: high ghost
+            const int r = t - side * 3 * across;
+            const int q = r / across, u = r - q * across;  // population slot, row / column
+            // low ghost: populations moving up the partition axis (+1), high: -1
+            const int i = px ? (side == 0 ? (q == 0 ? 0 : q == 1 ? 4 : 7)
+                                          : (q == 0 ? 2 : q == 1 ? 5 : 6))
+                             : (side == 0 ? (q == 0 ? 1 : q == 1 ? 4 : 5)
+                                          : (q == 0 ? 3 : q == 1 ? 6 : 7));
+            const int owner = side == 0 ? lo_owner : hi_owner;
+            const int src_g = side == 0 ? lo_src : hi_src;          // global column / row
+            const int src_l = src_g - owner * g.w;                  // in the owner's slab
+            float *mine = px ? at(b, i, side == 0 ? -1 : wx, u) : at(b, i, u, side == 0 ? -1 : wy);
+            float *theirs = px ? at(b, i, src_l, u) : at(b, i, u, src_l);
+            *mine = ld_cluster((uint32_t)__cvta_generic_to_shared(theirs), (unsigned)owner);
+        }
+    };
+
+    for (int l = threadIdx.x; l < count; l += blockDim.x) {
+        const int ly = l / wx, lx = l - ly * wx;
+        const long long node = (long long)(y0 + ly) * nx + (x0 + lx);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) *at(0, i, lx, ly) = src[(long long)i * plane + node];
+    }
+    cluster_sync();      // every slab loaded (and every CTA of the cluster running)
+    fill_ghosts(0);
+    __syncthreads();
+
+    // the neighbouring slabs this slab sends its edge nodes to, and where
+    const int lo_owner = px ? (x0 == 0 ? g.last_rank : rank - 1)
+                            : (y0 == 0 ? g.last_rank : rank - 1);
+    const int hi_owner = (px ? x0 + wx == nx : y0 + wy == ny) ? 0 : rank + 1;
+    const int last_w = (px ? nx : ny) - g.last_rank * g.w;      // the last slab's width
+    const int lo_w = (px ? x0 == 0 : y0 == 0) ? last_w : g.w;    // lo_owner's width
+
+    for (long s = 0; s < steps; ++s) {
+        const int a = (int)(s & 1), b = a ^ 1;
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            if (nly[j] < 0) continue;
+            const int lx = nlx[j], ly = nly[j];
+            // population i of node (sx, sy), which pull_node_with passes
+            // wrapped: one step along c_i from this node, so in the slab or
+            // its ghost on that side (a single slab wraps within itself)
+            auto load = [&](int i, int sx, int sy) -> float {
+                if (!ghosts) return *at(a, i, sx, sy);
+                return px ? *at(a, i, lx - cx_of(i), sy) : *at(a, i, sx, ly - cy_of(i));
+            };
+            float d[8];
+            pull_node_with(load, nx, ny, x0 + lx, y0 + ly, bc_x, bc_y, k, d);
+            collide(d, k);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) *at(b, i, lx, ly) = d[i];
+            if (ghosts) {
+                // edge nodes also go to the neighbours' ghosts of buffer b: the
+                // populations that move out of this slab towards them
+                auto send = [&](int i, int glx, int gly, int owner) {
+                    st_cluster((uint32_t)__cvta_generic_to_shared(at(b, i, glx, gly)),
+                               (unsigned)owner, d[i]);
+                };
+                if (px) {
+                    if (lx == 0) { send(2, lo_w, ly, lo_owner); send(5, lo_w, ly, lo_owner);
+                                   send(6, lo_w, ly, lo_owner); }
+                    if (lx == wx - 1) { send(0, -1, ly, hi_owner); send(4, -1, ly, hi_owner);
+                                        send(7, -1, ly, hi_owner); }
+                } else {
+                    if (ly == 0) { send(3, lx, lo_w, lo_owner); send(6, lx, lo_w, lo_owner);
+                                   send(7, lx, lo_w, lo_owner); }
+                    if (ly == wy - 1) { send(1, lx, -1, hi_owner); send(4, lx, -1, hi_owner);
+                                        send(5, lx, -1, hi_owner); }
+                }
+            }
+        }
+        // step s (and the ghosts it sent) complete everywhere before s + 1
+        if (ghosts) cluster_sync();
+        else __syncthreads();
+    }
+
+    // post-collision state of the last step (buffer steps & 1) and of the
+    // step before it (the other buffer)
+    const int last = (int)(steps & 1);
+    for (int l = threadIdx.x; l < count; l += blockDim.x) {
+        const int ly = l / wx, lx = l - ly * wx;
+        const long long node = (long long)(y0 + ly) * nx + (x0 + lx);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            out_last[(long long)i * plane + node] = *at(last, i, lx, ly);
+            out_prev[(long long)i * plane + node] = *at(last ^ 1, i, lx, ly);
+        }
+    }
+    // no CTA may leave while another can still read its shared memory
+    cluster_sync();
+}
+
+constexpr int MAX_CLUSTER = 16;
+constexpr int THREADS = 1024;
+constexpr int MAX_NPT = 4;            // nodes per thread
+constexpr int NODES_PER_CTA = 256;    // spread the lattice over up to 16 SMs
+
+struct DevState {
+    bool ready = false;
+    int optin = 0, cap = 0;
+};
+DevState g_dev[64];
+
+template <int NPT> constexpr auto kernel_npt() { return step_resident<NPT>; }
+using KernelFn = void (*)(const float *, float *, float *, long long, Slabs, int, int,
+                          Coef<float>, long);
+KernelFn kernel_of(int npt) {
+    switch (npt) {
+        case 1: return kernel_npt<1>();
+        case 2: return kernel_npt<2>();
+        case 3: return kernel_npt<3>();
+        default: return kernel_npt<4>();
+    }
+}
+
+// Once per device: clusters of up to 16 CTAs, and the largest dynamic
+// shared memory a plan may ask for (plans of several lattices coexist).
+cudaError_t prepare(int dev) {
+    DevState &d = g_dev[dev];
+    if (d.ready) return cudaSuccess;
+    cudaError_t e = cudaDeviceGetAttribute(&d.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    d.cap = d.optin - 1024;                           // bytes per CTA (some kept spare)
+    for (int npt = 1; npt <= MAX_NPT; ++npt) {
+        e = cudaFuncSetAttribute(kernel_of(npt), cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                 1);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kernel_of(npt), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 d.cap);
+        if (e != cudaSuccess) return e;
+    }
+    d.ready = true;
+    return cudaSuccess;
+}
+
+cudaLaunchConfig_t config_of(const ResidentPlan &p, cudaLaunchAttribute *attr,
+                             cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)p.cluster, 1, 1);
+    cfg.blockDim = dim3((unsigned)p.threads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)p.smem;
+    cfg.stream = stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)p.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+}  // namespace
+
+cudaError_t resident_plan(int precision, int nx, int ny, int cluster_req, ResidentPlan *out) {
+    *out = ResidentPlan{};
+    if (precision != PREC_FP32 || nx < 1 || ny < 1) return cudaErrorNotSupported;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if ((e = prepare(dev)) != cudaSuccess) return e;
+    const int cap = g_dev[dev].cap;
+    const long long plane = (long long)nx * ny;
+    const int part_x = nx >= ny ? 1 : 0;
+    const int extent = part_x ? nx : ny, across = part_x ? ny : nx;
+    const int most = std::min(MAX_CLUSTER, extent);   // at least one column (row) per CTA
+    // about NODES_PER_CTA nodes per CTA (the work of a step spread over up to
+    // 16 SMs), then larger clusters (less shared memory each), then smaller
+    int want = (int)std::min<long long>(most, (plane + NODES_PER_CTA - 1) / NODES_PER_CTA);
+    if (cluster_req > 0) want = std::min(cluster_req, most);
+    if (want < 1) want = 1;
+    int order[MAX_CLUSTER];
+    int n_order = 0;
+    for (int nr = want; nr <= most; ++nr) order[n_order++] = nr;
+    for (int nr = want - 1; nr >= 1; --nr) order[n_order++] = nr;
+    if (cluster_req > 0) n_order = 1;
+    for (int oi = 0; oi < n_order; ++oi) {
+        const int nr = order[oi];
+        const int w = (extent + nr - 1) / nr;
+        const long long nodes = (long long)w * across;              // per CTA, at most
+        const int threads = (int)std::min<long long>(THREADS, (nodes + 31) / 32 * 32);
+        const long long npt = (nodes + threads - 1) / threads;
+        if (npt > MAX_NPT) continue;
+        const int rows = part_x ? ny : w + 2, cols = part_x ? w + 2 : nx;
+        const long long bytes = 2LL * 8 * rows * cols * (long long)sizeof(float);
+        if (bytes > cap) continue;
+        ResidentPlan p;
+        p.cluster = nr;
+        p.part_x = part_x;
+        p.w = w;
+        p.rows = rows;
+        p.cols = cols;
+        p.last_rank = (extent - 1) / w;
+        p.npt = (int)npt;
+        p.threads = threads;
+        p.smem = (int)bytes;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = config_of(p, attr, nullptr);
+        int clusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&clusters, kernel_of(p.npt), &cfg);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (clusters < 1) continue;
+        *out = p;
+        return cudaSuccess;
+    }
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_resident(const float *src, float *out_last, float *out_prev, int nx, int ny,
+                            int bc_x, int bc_y, const Coef<float> &k, long steps,
+                            const ResidentPlan &p, cudaStream_t stream) {
+    if (p.cluster < 1 || p.npt < 1 || p.npt > MAX_NPT) return cudaErrorInvalidConfiguration;
+    if (steps < 1) return cudaSuccess;
+    Slabs g{nx, ny, p.part_x, p.w, p.rows, p.cols, p.cluster, p.last_rank};
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = config_of(p, attr, stream);
+    return cudaLaunchKernelEx(&cfg, kernel_of(p.npt), src, out_last, out_prev,
+                              (long long)nx * ny, g, bc_x, bc_y, k, steps);
+}
+
+}  // namespace plbm

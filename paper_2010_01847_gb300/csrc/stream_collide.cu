@@ -229,6 +229,9 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
     // a step that also reduces the residual (one step in many) runs on the
     // vector kernel, whose warps read the history planes with 16-byte vectors
     if (kernel == KERNEL_STAGED && rq) kernel = KERNEL_VECTOR;
+    // single steps of a cluster-resident lattice (the residual step) run on
+    // the vector kernel when nx allows, else the scalar one
+    if (kernel == KERNEL_RESIDENT) kernel = nx % Pack<T>::V == 0 ? KERNEL_VECTOR : KERNEL_SCALAR;
     if (kernel == KERNEL_STAGED)
         return launch_step_staged<T>(src, dst, nx, ny, bc_x, bc_y, k, status, plan, blocks_out,
                                      stream);
@@ -272,6 +275,8 @@ long long step_blocks(int kernel, int precision, int nx, int ny, const StagedPla
     const long long plane = (long long)nx * ny;
     (void)plan;
     if (kernel == KERNEL_STAGED) kernel = KERNEL_VECTOR;    // residual steps run there
+    if (kernel == KERNEL_RESIDENT)
+        kernel = nx % vector_width(precision) == 0 ? KERNEL_VECTOR : KERNEL_SCALAR;
     const long long threads = kernel == KERNEL_VECTOR ? plane / vector_width(precision) : plane;
     const int bs = step_block_size(threads);
     return (threads + bs - 1) / bs;

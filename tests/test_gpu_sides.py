@@ -68,11 +68,13 @@ VEC = {"fp32": 4, "fp64": 2, "fp16": 8, "bf16": 8}
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16", "bf16"])
-@pytest.mark.parametrize("kernel", ["scalar", "vector"])
+@pytest.mark.parametrize("kernel", ["scalar", "vector", "resident"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
 def test_sides_parity(case, kernel, precision):
     if kernel == "vector" and case[1] % VEC[precision]:
         pytest.skip(f"nx = {case[1]} is not a multiple of the vector width")
+    if kernel == "resident" and precision != "fp32":
+        pytest.skip("the cluster-resident kernel stores FP32")
     g, o = _pair(case, precision, kernel=kernel)
     assert g.kernel == kernel
     for steps in (1, 57):
@@ -152,14 +154,17 @@ def test_sides_vector_equals_scalar_bitwise():
 
 
 def test_sides_kernel_choice_and_errors():
-    lat = plbm.Lattice(64, 16, 0.9, 15.0, S, plbm.PERIODIC)
+    # FP32 lattices of up to 16384 nodes run cluster-resident by default
+    assert plbm.Lattice(64, 16, 0.9, 15.0, S, plbm.PERIODIC).kernel == "resident"
+    assert plbm.Lattice(64, 16, 0.9, 15.0, S, plbm.PERIODIC, precision="fp64").kernel == "vector"
+    lat = plbm.Lattice(512, 64, 0.9, 15.0, S, plbm.PERIODIC)
     assert lat.kernel == "vector"                    # nx a multiple of the vector width
     with pytest.raises(plbm.LBMError) as ei:
         lat.set_kernel("staged")
     assert ei.value.status == plbm.EUNSUPPORTED
     lat.set_kernel("scalar")
     assert lat.kernel == "scalar"
-    ragged = plbm.Lattice(37, 16, 0.9, 15.0, S, plbm.PERIODIC)
+    ragged = plbm.Lattice(517, 64, 0.9, 15.0, S, plbm.PERIODIC)
     assert ragged.kernel == "scalar"
     with pytest.raises(plbm.LBMError) as ei:
         ragged.set_kernel("vector")
@@ -173,9 +178,9 @@ def test_sides_kernel_choice_and_errors():
     with pytest.raises(plbm.LBMError) as ei:
         lat.set_side(plbm.LEFT, ISO, math.nan)
     assert ei.value.status == plbm.EINVAL
-    lat.init(np.ones((16, 64)))
+    lat.init(np.ones((64, 512)))
     lat.autotune(4)
-    assert lat.kernel in ("scalar", "vector")
+    assert lat.kernel in ("scalar", "vector", "resident")
     # batches take periodic / gradient / walls only
     with pytest.raises(plbm.LBMError) as ei:
         plbm.Batch([dict(nx=64, ny=16, tau_N=0.9, tau_R=15.0, bc_x=S,
