@@ -33,6 +33,13 @@ CASES = [
      [(plbm.ISOTHERMAL, 1.0), (plbm.ISOTHERMAL, 1.0), (plbm.ISOTHERMAL, 1.0),
       (plbm.HEAT_FLUX, 1e-4)]),
     (401, 3, S, plbm.PERIODIC, 0.0, "scalar", "fp16", [(plbm.HEAT_FLUX, 1e-4), (plbm.DIFFUSE, 0)]),
+    # cluster-resident: column slabs (16 CTAs, ragged last slab), row slabs, one CTA
+    (201, 201, S, S, 0.0, "resident", "fp32",
+     [(plbm.ISOTHERMAL, 1.0), (plbm.ISOTHERMAL, 1.0), (plbm.ISOTHERMAL, 1.0),
+      (plbm.HEAT_FLUX, 1e-4)]),
+    (17, 1000, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3, "resident", "fp32", None),
+    (37, 29, plbm.PERIODIC, plbm.PERIODIC, 0.0, "resident", "fp32", None),
+    (8, 2, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3, "resident", "fp32", None),
 ]
 
 
