@@ -149,27 +149,87 @@ step_resident(const float *src, float *out_last, float *out_prev, long long plan
     const int last_w = (px ? nx : ny) - g.last_rank * g.w;      // the last slab's width
     const int lo_w = (px ? x0 == 0 : y0 == 0) ? last_w : g.w;    // lo_owner's width
 
+    // Each node's pull, worked out once for the whole launch with the rules
+    // of pull_node_with (lbm_device.cuh): for population i the offset of its
+    // source within a plane (own slab, ghost, or wrapped within a single
+    // slab), whether it is unknown (beyond a wall or side: filled by Eq. 58 /
+    // Section 2.5), and whether the node's pulls cross the seam (Eqs. 59-60).
+    // info bits: 0-7 unknown i; 8 seam at x = 0 (+jump on c_x = +1); 9 seam
+    // at x = nx - 1 (-jump on c_x = -1); 10 / 11 wall row bottom / top;
+    // 12-15 on the left / right / bottom / top side.
+    const bool walls = bc_y == BC_WALLS;
+    const bool sides_x = bc_x == BC_SIDES, sides_y = bc_y == BC_SIDES;
+    const bool open_y = walls || sides_y, grad = bc_x == BC_GRADIENT;
+    const int pb = g.rows * g.cols;                 // one plane of a slab buffer
+    unsigned rel[NPT][4], info[NPT];
+    int own[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int lx = nlx[j], ly = nly[j], x = x0 + lx, y = y0 + ly;
+        own[j] = (ly + gy) * g.cols + (lx + gx);
+        unsigned f = 0;
+        if (grad && x == 0) f |= 1u << 8;
+        if (grad && x == nx - 1) f |= 1u << 9;
+        if (walls && y == 0) f |= 1u << 10;
+        if (walls && y == ny - 1) f |= 1u << 11;
+        if (sides_x && x == 0) f |= 1u << 12;
+        if (sides_x && x == nx - 1) f |= 1u << 13;
+        if (sides_y && y == 0) f |= 1u << 14;
+        if (sides_y && y == ny - 1) f |= 1u << 15;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int cx = cx_of(i), cy = cy_of(i);
+            int sy = y - cy, sx = x - cx;
+            const bool unknown = (open_y && (sy < 0 || sy >= ny)) ||
+                                 (sides_x && (sx < 0 || sx >= nx));
+            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+            sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+            int qx = sx, qy = sy;                    // source in local coordinates
+            if (ghosts) {
+                if (px) qx = lx - cx;
+                else qy = ly - cy;
+            }
+            const unsigned r = unknown ? 0u : (unsigned)((qy + gy) * g.cols + (qx + gx));
+            if (unknown) f |= 1u << i;
+            if (i & 1) rel[j][i >> 1] |= r << 16;
+            else rel[j][i >> 1] = r;
+        }
+        info[j] = nly[j] < 0 ? 0u : f;
+    }
+
     for (long s = 0; s < steps; ++s) {
-        const int a = (int)(s & 1), b = a ^ 1;
+        const float *A = sm + (s & 1) * 8 * pb;
+        float *B = sm + ((s & 1) ^ 1) * 8 * pb;
+        const int b = (int)((s & 1) ^ 1);
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             if (nly[j] < 0) continue;
-            const int lx = nlx[j], ly = nly[j];
-            // population i of node (sx, sy), which pull_node_with passes
-            // wrapped: one step along c_i from this node, so in the slab or
-            // its ghost on that side (a single slab wraps within itself)
-            auto load = [&](int i, int sx, int sy) -> float {
-                if (!ghosts) return *at(a, i, sx, sy);
-                return px ? *at(a, i, lx - cx_of(i), sy) : *at(a, i, sx, ly - cy_of(i));
-            };
+            const unsigned f = info[j];
             float d[8];
-            pull_node_with(load, nx, ny, x0 + lx, y0 + ly, bc_x, bc_y, k, d);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (f & (1u << i)) {
+                    d[i] = 0.f;
+                } else {
+                    const unsigned r = (i & 1) ? rel[j][i >> 1] >> 16 : rel[j][i >> 1] & 0xffffu;
+                    float jump = 0.f;             // added as pull_node_with adds it
+                    if (cx_of(i) > 0 && (f & (1u << 8))) jump = i < 4 ? k.jump_axis : k.jump_diag;
+                    if (cx_of(i) < 0 && (f & (1u << 9)))
+                        jump = -(i < 4 ? k.jump_axis : k.jump_diag);
+                    d[i] = A[i * pb + (int)r] + jump;
+                }
+            }
+            if (f & (1u << 10)) wall_bottom(d, k);
+            if (f & (1u << 11)) wall_top(d, k);
+            if (f & (0xfu << 12))
+                apply_sides(d, k, (f >> 12) & 1u, (f >> 13) & 1u, (f >> 14) & 1u, (f >> 15) & 1u);
             collide(d, k);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) *at(b, i, lx, ly) = d[i];
+            for (int i = 0; i < 8; ++i) B[i * pb + own[j]] = d[i];
             if (ghosts) {
                 // edge nodes also go to the neighbours' ghosts of buffer b: the
                 // populations that move out of this slab towards them
+                const int lx = nlx[j], ly = nly[j];
                 auto send = [&](int i, int glx, int gly, int owner) {
                     st_cluster((uint32_t)__cvta_generic_to_shared(at(b, i, glx, gly)),
                                (unsigned)owner, d[i]);
