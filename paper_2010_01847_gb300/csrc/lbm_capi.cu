@@ -346,6 +346,11 @@ int resolve_kernel(lbm_ctx *c, int requested) {
     if (requested == KERNEL_AUTO && c->precision == PREC_FP32 &&
         c->plane <= RESIDENT_AUTO_NODES && resident_ok(c))
         return KERNEL_RESIDENT;
+    // small FP64 lattices: FP64 arithmetic bounds the step, and one node per
+    // thread spreads it over twice the SMs of the 2-node vectors (128 x 32:
+    // 5.3-5.6 against 6.2 us per step)
+    if (requested == KERNEL_AUTO && c->precision == PREC_FP64 && c->plane <= RESIDENT_AUTO_NODES)
+        return KERNEL_SCALAR;
     if (has_sides(c)) {     // the per-side rules: scalar, vector and resident kernels
         if (requested == KERNEL_AUTO) return vec_ok ? KERNEL_VECTOR : KERNEL_SCALAR;
         if (requested == KERNEL_SCALAR) return KERNEL_SCALAR;

@@ -154,9 +154,10 @@ def test_sides_vector_equals_scalar_bitwise():
 
 
 def test_sides_kernel_choice_and_errors():
-    # FP32 lattices of up to 16384 nodes run cluster-resident by default
+    # FP32 lattices of up to 16384 nodes run cluster-resident by default, FP64
+    # ones one node per thread
     assert plbm.Lattice(64, 16, 0.9, 15.0, S, plbm.PERIODIC).kernel == "resident"
-    assert plbm.Lattice(64, 16, 0.9, 15.0, S, plbm.PERIODIC, precision="fp64").kernel == "vector"
+    assert plbm.Lattice(64, 16, 0.9, 15.0, S, plbm.PERIODIC, precision="fp64").kernel == "scalar"
     lat = plbm.Lattice(512, 64, 0.9, 15.0, S, plbm.PERIODIC)
     assert lat.kernel == "vector"                    # nx a multiple of the vector width
     with pytest.raises(plbm.LBMError) as ei:
