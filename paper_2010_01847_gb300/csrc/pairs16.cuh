@@ -79,12 +79,19 @@ struct SeamAdd {
     bool left, left_jump, right, right_jump;
 };
 
+// Does nothing with a node pair's pulled state (the plain step).
+struct NoPairHook {
+    __device__ __forceinline__ void operator()(int, const float2 (&)[8]) const {}
+};
+
 // Walls (Eq. 58 on the bottom / top row), collision, and repacking of the 8
 // nodes held in w (after the shift), in place: word m of w[i] becomes the
-// post-collision values of nodes 2m, 2m + 1 of population i.
-template <typename T>
+// post-collision values of nodes 2m, 2m + 1 of population i.  hook(m, f)
+// sees each pair's pulled state (after the walls, before the collision).
+template <typename T, typename Hook = NoPairHook>
 __device__ __forceinline__ void collide_words16(uint4 (&w)[8], const Coef<float> &k,
-                                                const SeamAdd &seam, bool bottom, bool top) {
+                                                const SeamAdd &seam, bool bottom, bool top,
+                                                const Hook &hook = Hook()) {
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         float2 f[8];
@@ -106,6 +113,7 @@ __device__ __forceinline__ void collide_words16(uint4 (&w)[8], const Coef<float>
         }
         if (bottom) wall_bottom(f, k);
         if (top) wall_top(f, k);
+        hook(m, f);
         collide_f32<float2>(f, k);
 #pragma unroll
         for (int i = 0; i < 8; ++i) set_word(w[i], m, f2_to_word<T>(f[i]));

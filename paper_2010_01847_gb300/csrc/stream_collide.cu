@@ -193,6 +193,95 @@ step_vector16(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, lo
     for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, w[i]);
 }
 
+// The same step that also reduces the residual of the pulled state
+// (residual_terms on each node in node order, the history planes read and
+// written as node pairs): the sums the node-by-node kernel forms.  A kernel
+// of its own rather than a template flag on step_vector16: the plain step's
+// register allocation, and with it its speed, moved when the two shared one
+// body (358 against 331 us per step at 8192^2).
+template <typename T>
+__global__ void __launch_bounds__(256, 3)
+step_vector16_res(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
+                  long long plane, int bc_x, int bc_y, Coef<float> k, ResidualReq<float> rq) {
+    static_assert(sizeof(T) == 2 && Pack<T>::V == 8, "16-bit storage");
+    constexpr int V = 8;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int tpr = nx / V;
+    const long long total = (long long)tpr * ny;
+    const bool active = t < total;
+    const int y = active ? int(t / tpr) : 0;
+    const int xv = active ? int(t - (long long)y * tpr) : 0;
+    const int x0 = xv * V;
+    const int lane = threadIdx.x & 31;
+    const bool walls = bc_y == BC_WALLS;
+    const bool bottom = walls && y == 0;
+    const bool top = walls && y == ny - 1;
+    const bool need_left = (lane == 0 || xv == 0) && active;
+    const bool need_right = (lane == 31 || xv + 1 == tpr) && active;
+    const int sx_left = x0 == 0 ? nx - 1 : x0 - 1;
+    const int sx_right = x0 + V >= nx ? x0 + V - nx : x0 + V;
+
+    uint4 w[8];
+    unsigned edge[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i);
+        int sy = y - cy;
+        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+        const long long row = (long long)i * plane + (long long)sy * nx;
+        const bool unknown = (cy > 0 && bottom) || (cy < 0 && top);
+        w[i] = (active && !unknown) ? ld_stream(src + row + x0) : make_uint4(0u, 0u, 0u, 0u);
+        edge[i] = 0u;
+        if (cx > 0 && need_left && !unknown) edge[i] = ld_u16(src + row + sx_left);
+        if (cx < 0 && need_right && !unknown) edge[i] = ld_u16(src + row + sx_right);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int cx = cx_of(i);
+        if (cx > 0) {
+            unsigned nb = __shfl_up_sync(0xffffffffu, w[i].w, 1);
+            if (need_left) nb = edge[i] << 16;
+            w[i] = shift_from_left(w[i], nb);
+        } else if (cx < 0) {
+            unsigned nb = __shfl_down_sync(0xffffffffu, w[i].x, 1);
+            if (need_right) nb = edge[i];
+            w[i] = shift_from_right(w[i], nb);
+        }
+    }
+    float loc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (active) {
+        const bool grad = bc_x == BC_GRADIENT;
+        const SeamAdd seam{need_left, x0 == 0 && grad, need_right, x0 + V == nx && grad};
+        const long long out = (long long)y * nx + x0;
+        const bool have_prev = rq.have_prev != 0;
+        auto residual = [&](int m, const float2 (&f)[8]) {
+            float2 h[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                h[q] = have_prev
+                           ? *reinterpret_cast<const float2 *>(rq.prev + q * plane + out + 2 * m)
+                           : make_float2(0.f, 0.f);
+            float n0[8], n1[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                n0[i] = f[i].x;
+                n1[i] = f[i].y;
+            }
+            residual_terms(n0, k, rq.inv_scale, h[0].x, h[1].x, h[2].x, have_prev, loc);
+            residual_terms(n1, k, rq.inv_scale, h[0].y, h[1].y, h[2].y, have_prev, loc);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                *reinterpret_cast<float2 *>(rq.prev + q * plane + out + 2 * m) = h[q];
+        };
+        collide_words16<T>(w, k, seam, bottom, top, residual);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, w[i]);
+    }
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    warp_flush_residual(loc, acc);
+    block_sum5_lane0(acc, rq.partials + (size_t)blockIdx.x * 5);
+}
+
 // ---------------------------------------------------------------------------
 // Threads per block of a step launch: 256, or fewer (a multiple of 32) when
 // the lattice is small, so that the launch still spreads over every SM: a
@@ -250,8 +339,12 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
                                                                    bc_y, k, none);
     } else if (kernel == KERNEL_VECTOR) {
         if (rq) {
-            step_vector<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
-                                                            k, *rq);
+            if constexpr (sizeof(T) == 2)
+                step_vector16_res<T><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                                bc_y, k, *rq);
+            else
+                step_vector<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                                bc_y, k, *rq);
         } else {
             if constexpr (sizeof(T) == 2)
                 step_vector16<T><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
