@@ -422,6 +422,9 @@ def run_native(args):
         out = [torch.empty((ny, nx), dtype=torch.float64).pin_memory() for _ in range(3)]
         hp = host.numpy()
         op = [o.numpy() for o in out]
+        # pinning ~2 GB above leaves the GPU idle for a while: warm it up
+        # again, untimed, as before the device-timed region
+        chunked(max(args.warmup, 3))
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
