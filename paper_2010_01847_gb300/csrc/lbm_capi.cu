@@ -207,7 +207,7 @@ template <typename T> struct StepOp {
             if (c->kernel == KERNEL_RESIDENT)     // one step: last -> dst, previous -> src
                 return launch_resident((const float *)c->buf[src], (float *)c->buf[1 - src],
                                        (float *)c->buf[src], c->nx, c->ny, c->bc_x, c->bc_y,
-                                       make_coef<float>(c), 1, c->rplan, s);
+                                       make_coef<float>(c), 1, c->rplan, status_word(c), s);
         return launch_step<T>(c->kernel, (const T *)c->buf[src], (T *)c->buf[1 - src], c->nx,
                               c->ny, c->bc_x, c->bc_y, make_coef<C>(c), status_word(c), nullptr,
                               c->plan, nullptr, s);
@@ -298,7 +298,10 @@ lbm_status check_status(lbm_ctx *c) {
     if (!c->aux) return LBM_OK;
     int st = 0;
     CK(c, cudaMemcpy(&st, status_word(c), sizeof(int), cudaMemcpyDeviceToHost));
-    if (st) return fail(c, LBM_ETIMEOUT, "a bounded device-side wait gave up (staged kernel)");
+    if (st)
+        return fail(c, LBM_ETIMEOUT,
+                    (st & 2) ? "a bounded device-side wait gave up (cluster-resident kernel)"
+                             : "a bounded device-side wait gave up (staged kernel)");
     return LBM_OK;
 }
 
@@ -619,7 +622,7 @@ lbm_status lbm_step(lbm_ctx *c, long n) {
         const int last = c->cur ^ (int)(n & 1);
         CK(c, launch_resident((const float *)c->buf[c->cur], (float *)c->buf[last],
                               (float *)c->buf[last ^ 1], c->nx, c->ny, c->bc_x, c->bc_y,
-                              make_coef<float>(c), n, c->rplan, c->stream));
+                              make_coef<float>(c), n, c->rplan, status_word(c), c->stream));
         c->cur = last;
         c->n += n;
         c->launches += 1;
@@ -952,11 +955,11 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
             const Coef<float> kf = make_coef<float>(c);
             float *b0 = (float *)c->buf[0], *b1 = (float *)c->buf[1];
             err = launch_resident(b0, b0, b1, c->nx, c->ny, c->bc_x, c->bc_y, kf, 2, c->rplan,
-                                  c->stream);
+                                  status_word(c), c->stream);
             if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
             if (err == cudaSuccess)
                 err = launch_resident(b0, b0, b1, c->nx, c->ny, c->bc_x, c->bc_y, kf,
-                                      trial_steps, c->rplan, c->stream);
+                                      trial_steps, c->rplan, status_word(c), c->stream);
         } else {
             for (int s = 0; s < 2 && err == cudaSuccess; ++s)      // warm-up
                 err = dispatch<StepOp>(c, s & 1, c->stream);

@@ -89,10 +89,11 @@ cudaError_t resident_plan(int precision, int nx, int ny, int cluster_req, Reside
 // `steps` (>= 1) time steps from the post-collision planes `src`: writes the
 // post-collision planes of the last step to out_last and of the step before
 // it to out_prev (src may be either; each CTA reads its own nodes before it
-// writes them).
+// writes them).  `status`: the device word a bounded wait that gives up sets
+// (bit 2).
 cudaError_t launch_resident(const float *src, float *out_last, float *out_prev, int nx, int ny,
                             int bc_x, int bc_y, const Coef<float> &k, long steps,
-                            const ResidentPlan &p, cudaStream_t stream);
+                            const ResidentPlan &p, int *status, cudaStream_t stream);
 
 // Runs the staged kernel's bounded mbarrier wait against a barrier nothing
 // completes (one CTA, ~2 s); the wait gives up and ORs 1 into *status.

@@ -8,21 +8,24 @@
 // one launch per step costs more than the step.  Here one cluster of up to
 // 16 CTAs holds both post-collision buffers (8 planes each) in shared
 // memory.  CTA r owns a slab of the lattice (columns [r w, (r + 1) w) when
-// nx >= ny, else rows); each step every CTA pulls its nodes from the
-// current buffer -- its own slab from its shared memory, the neighbours'
-// edge nodes from theirs through distributed shared memory
-// (ld.shared::cluster) -- applies the seam jump, walls and sides, collides
-// (the same pull_node_with / collide as every other kernel: identical bits)
-// and writes the other buffer in its own shared memory; one cluster barrier
-// per step orders the writes of step n before the reads of step n + 1.
+// nx >= ny, else rows) plus one ghost column (row) on each side.  Each step
+// every CTA pulls its nodes from the current buffer (its slab and ghosts),
+// applies the seam jump, walls and sides (each node's pull worked out once
+// per launch with the rules of pull_node_with), collides (the collide of
+// every other kernel: identical bits) and writes the other buffer; its edge
+// nodes also send the populations that leave the slab into the neighbours'
+// ghosts with asynchronous remote stores (st.async through distributed
+// shared memory) that count their bytes on an mbarrier of the receiver.
+// Before the next step a CTA waits only for its own ghost bytes (and its own
+// threads, __syncthreads): no cluster-wide barrier per step.
 // Global memory is read once at the start and written once at the end:
 // post-collision state of the last step and of the one before it, as
 // step-by-step launches would leave them (the read-outs pull from the
 // latter).
 //
-// The barrier is the hardware cluster barrier; every thread of every CTA
-// reaches it once per step (uniform loop bounds, no early exit), so no wait
-// depends on data.
+// Every mbarrier wait is bounded (about 2 s) and reports through a status
+// word (LBM_ETIMEOUT); the only cluster barriers are the one after the
+// initial load and the one before exit, which every thread reaches.
 #include <algorithm>
 
 #include "lbm_kernels.h"
@@ -51,10 +54,54 @@ __device__ __forceinline__ float ld_cluster(uint32_t local_addr, unsigned rank) 
     return v;
 }
 
-__device__ __forceinline__ void st_cluster(uint32_t local_addr, unsigned rank, float v) {
+// Ghost exchange between neighbouring CTAs: each edge node sends the
+// populations that leave its slab with an asynchronous remote store whose
+// completion counts bytes on an mbarrier of the receiving CTA; the receiver
+// waits for its bytes (bounded) before it next pulls from its ghosts.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t map_to(uint32_t local_addr, unsigned rank) {
     uint32_t remote;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(v) : "memory");
+    return remote;
+}
+__device__ __forceinline__ void st_async(uint32_t remote_addr, float v, uint32_t remote_bar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
+            remote_addr),
+        "r"(__float_as_uint(v)), "r"(remote_bar)
+        : "memory");
+}
+__device__ __forceinline__ void bar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (iteration and clock limits, ~2 s): a wait that gives up
+// sets bit 2 of *status (read back as LBM_ETIMEOUT) and returns.
+__device__ __forceinline__ void bar_wait(uint64_t *bar, uint32_t parity, int *status) {
+    if (bar_try(bar, parity)) return;
+    const long long t0 = clock64();
+    for (long long it = 0; it < (1LL << 28); ++it) {
+        if (bar_try(bar, parity)) return;
+        if ((it & 255) == 255 && clock64() - t0 > 4000000000LL) break;
+    }
+    atomicOr(status, 2);
 }
 
 // Slab geometry shared by every CTA of the cluster.  A slab is stored with
@@ -73,9 +120,12 @@ struct Slabs {
 template <int NPT>
 __global__ void __launch_bounds__(1024, 1)
 step_resident(const float *src, float *out_last, float *out_prev, long long plane, Slabs g,
-              int bc_x, int bc_y, Coef<float> k, long steps) {
+              int bc_x, int bc_y, Coef<float> k, long steps, int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *sm = reinterpret_cast<float *>(smem_raw);
+    // after the two buffers: one mbarrier per buffer for its incoming ghosts
+    uint64_t *full = reinterpret_cast<uint64_t *>(
+        smem_raw + (((size_t)16 * g.rows * g.cols * sizeof(float) + 15) & ~(size_t)15));
     const int rank = (int)cluster_rank();
     const int nx = g.nx, ny = g.ny;
     const bool px = g.part_x != 0;
@@ -132,13 +182,20 @@ step_resident(const float *src, float *out_last, float *out_prev, long long plan
         }
     };
 
+    if (threadIdx.x == 0) {
+        bar_init(&full[0]);
+        bar_init(&full[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     for (int l = threadIdx.x; l < count; l += blockDim.x) {
         const int ly = l / wx, lx = l - ly * wx;
         const long long node = (long long)(y0 + ly) * nx + (x0 + lx);
 #pragma unroll
         for (int i = 0; i < 8; ++i) *at(0, i, lx, ly) = src[(long long)i * plane + node];
     }
-    cluster_sync();      // every slab loaded (and every CTA of the cluster running)
+    // every slab loaded and every barrier initialised (and every CTA of the
+    // cluster running) before any CTA reads or writes another's
+    cluster_sync();
     fill_ghosts(0);
     __syncthreads();
 
@@ -197,10 +254,27 @@ step_resident(const float *src, float *out_last, float *out_prev, long long plan
         info[j] = nly[j] < 0 ? 0u : f;
     }
 
+    // bytes of ghosts the two neighbours send into this slab per step: 3
+    // populations of every node of their edge column (row) each
+    const uint32_t ghost_bytes = 2u * 3u * (uint32_t)(px ? ny : nx) * (uint32_t)sizeof(float);
+    const bool exchange = ghosts && count > 0;
+    // the neighbours' barriers of buffers 0 and 1
+    uint32_t lo_bar0 = 0u, lo_bar1 = 0u, hi_bar0 = 0u, hi_bar1 = 0u;
+    if (exchange) {
+        lo_bar0 = map_to(smem_u32(&full[0]), (unsigned)lo_owner);
+        lo_bar1 = map_to(smem_u32(&full[1]), (unsigned)lo_owner);
+        hi_bar0 = map_to(smem_u32(&full[0]), (unsigned)hi_owner);
+        hi_bar1 = map_to(smem_u32(&full[1]), (unsigned)hi_owner);
+    }
+
     for (long s = 0; s < steps; ++s) {
         const float *A = sm + (s & 1) * 8 * pb;
         float *B = sm + ((s & 1) ^ 1) * 8 * pb;
         const int b = (int)((s & 1) ^ 1);
+        // ghosts are exchanged for the steps that follow within this launch
+        const bool more = s + 1 < steps;
+        const uint32_t lo_bar = b ? lo_bar1 : lo_bar0, hi_bar = b ? hi_bar1 : hi_bar0;
+        if (exchange && more && threadIdx.x == 0) bar_expect(&full[b], ghost_bytes);
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             if (nly[j] < 0) continue;
@@ -226,30 +300,37 @@ step_resident(const float *src, float *out_last, float *out_prev, long long plan
             collide(d, k);
 #pragma unroll
             for (int i = 0; i < 8; ++i) B[i * pb + own[j]] = d[i];
-            if (ghosts) {
+            if (exchange && more) {
                 // edge nodes also go to the neighbours' ghosts of buffer b: the
                 // populations that move out of this slab towards them
                 const int lx = nlx[j], ly = nly[j];
-                auto send = [&](int i, int glx, int gly, int owner) {
-                    st_cluster((uint32_t)__cvta_generic_to_shared(at(b, i, glx, gly)),
-                               (unsigned)owner, d[i]);
+                auto send = [&](int i, int glx, int gly, int owner, uint32_t bar) {
+                    st_async(map_to(smem_u32(at(b, i, glx, gly)), (unsigned)owner), d[i], bar);
                 };
                 if (px) {
-                    if (lx == 0) { send(2, lo_w, ly, lo_owner); send(5, lo_w, ly, lo_owner);
-                                   send(6, lo_w, ly, lo_owner); }
-                    if (lx == wx - 1) { send(0, -1, ly, hi_owner); send(4, -1, ly, hi_owner);
-                                        send(7, -1, ly, hi_owner); }
+                    if (lx == 0) { send(2, lo_w, ly, lo_owner, lo_bar);
+                                   send(5, lo_w, ly, lo_owner, lo_bar);
+                                   send(6, lo_w, ly, lo_owner, lo_bar); }
+                    if (lx == wx - 1) { send(0, -1, ly, hi_owner, hi_bar);
+                                        send(4, -1, ly, hi_owner, hi_bar);
+                                        send(7, -1, ly, hi_owner, hi_bar); }
                 } else {
-                    if (ly == 0) { send(3, lx, lo_w, lo_owner); send(6, lx, lo_w, lo_owner);
-                                   send(7, lx, lo_w, lo_owner); }
-                    if (ly == wy - 1) { send(1, lx, -1, hi_owner); send(4, lx, -1, hi_owner);
-                                        send(5, lx, -1, hi_owner); }
+                    if (ly == 0) { send(3, lx, lo_w, lo_owner, lo_bar);
+                                   send(6, lx, lo_w, lo_owner, lo_bar);
+                                   send(7, lx, lo_w, lo_owner, lo_bar); }
+                    if (ly == wy - 1) { send(1, lx, -1, hi_owner, hi_bar);
+                                        send(4, lx, -1, hi_owner, hi_bar);
+                                        send(5, lx, -1, hi_owner, hi_bar); }
                 }
             }
         }
-        // step s (and the ghosts it sent) complete everywhere before s + 1
-        if (ghosts) cluster_sync();
-        else __syncthreads();
+        // this CTA's writes of step s before any of its threads reads them
+        __syncthreads();
+        // and the neighbours' ghosts of buffer b, the (s >> 1)-th use of its
+        // barrier.  A neighbour writes these ghosts again only two steps
+        // later, after it has received this CTA's edge nodes of step s + 1,
+        // which are sent after they were pulled from the ghosts.
+        if (exchange && more) bar_wait(&full[b], (uint32_t)((s >> 1) & 1), status);
     }
 
     // post-collision state of the last step (buffer steps & 1) and of the
@@ -264,7 +345,8 @@ step_resident(const float *src, float *out_last, float *out_prev, long long plan
             out_prev[(long long)i * plane + node] = *at(last ^ 1, i, lx, ly);
         }
     }
-    // no CTA may leave while another can still read its shared memory
+    // no CTA may leave while another can still read its shared memory (the
+    // last step sends no ghosts, so no remote store is in flight)
     cluster_sync();
 }
 
@@ -281,7 +363,7 @@ DevState g_dev[64];
 
 template <int NPT> constexpr auto kernel_npt() { return step_resident<NPT>; }
 using KernelFn = void (*)(const float *, float *, float *, long long, Slabs, int, int,
-                          Coef<float>, long);
+                          Coef<float>, long, int *);
 KernelFn kernel_of(int npt) {
     switch (npt) {
         case 1: return kernel_npt<1>();
@@ -360,7 +442,9 @@ cudaError_t resident_plan(int precision, int nx, int ny, int cluster_req, Reside
         const long long npt = (nodes + threads - 1) / threads;
         if (npt > MAX_NPT) continue;
         const int rows = part_x ? ny : w + 2, cols = part_x ? w + 2 : nx;
-        const long long bytes = 2LL * 8 * rows * cols * (long long)sizeof(float);
+        // two buffers, then two mbarriers (16-byte aligned)
+        const long long bytes =
+            ((2LL * 8 * rows * cols * (long long)sizeof(float) + 15) & ~15LL) + 16;
         if (bytes > cap) continue;
         ResidentPlan p;
         p.cluster = nr;
@@ -389,14 +473,14 @@ cudaError_t resident_plan(int precision, int nx, int ny, int cluster_req, Reside
 
 cudaError_t launch_resident(const float *src, float *out_last, float *out_prev, int nx, int ny,
                             int bc_x, int bc_y, const Coef<float> &k, long steps,
-                            const ResidentPlan &p, cudaStream_t stream) {
+                            const ResidentPlan &p, int *status, cudaStream_t stream) {
     if (p.cluster < 1 || p.npt < 1 || p.npt > MAX_NPT) return cudaErrorInvalidConfiguration;
     if (steps < 1) return cudaSuccess;
     Slabs g{nx, ny, p.part_x, p.w, p.rows, p.cols, p.cluster, p.last_rank};
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = config_of(p, attr, stream);
     return cudaLaunchKernelEx(&cfg, kernel_of(p.npt), src, out_last, out_prev,
-                              (long long)nx * ny, g, bc_x, bc_y, k, steps);
+                              (long long)nx * ny, g, bc_x, bc_y, k, steps, status);
 }
 
 }  // namespace plbm
