@@ -500,6 +500,21 @@ lbm_status lbm_residual_noalloc(const double *e, const double *qx, const double 
  * Errors: ECUDA (text from lbm_last_error(NULL)). */
 lbm_status lbm_check_bounded_wait(void *stream, int *gave_up, double *seconds);
 
+/* Self-check of the failure path of the cluster-resident kernel's ghost
+ * exchange (no counterpart in the paper).  Each CTA of that kernel waits,
+ * bounded by an iteration count and a clock limit (about 2 s), for the
+ * bytes its neighbours store into its ghost cells; a wait that gives up
+ * sets bit 2 of the context's status word, and every CTA of the launch then
+ * stops stepping, writes nothing and leaves, so one stalled exchange costs
+ * one wait limit per launch.  This call runs that same wait, in one thread
+ * of a one-CTA cluster, on a fresh barrier that nothing completes,
+ * asynchronously on the context's stream with the context's status word:
+ * the next synchronising call on ctx (lbm_sync, lbm_moments, ...) returns
+ * LBM_ETIMEOUT naming the cluster-resident kernel.  The context's state is
+ * untouched; lbm_init (or lbm_set_state) clears the status word.
+ * Errors: EINVAL (NULL ctx), ENOMEM, ECUDA. */
+lbm_status lbm_probe_resident_wait(lbm_ctx *ctx);
+
 /* ------------------------------------------------------------------------ *
  * The D1Q2 and D3Q14 lattices (periodic lattices only).
  *

@@ -51,7 +51,7 @@ EXPORTS = [
     "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_param_count", "lbm_mlp_set_params",
     "lbm_mlp_get_params", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train_step",
     "lbm_mlp_last_error",
-    "lbm_residual_noalloc", "lbm_check_bounded_wait",
+    "lbm_residual_noalloc", "lbm_check_bounded_wait", "lbm_probe_resident_wait",
     "lbm_nd_lattice_speed", "lbm_nd_create", "lbm_nd_init", "lbm_nd_step", "lbm_nd_sync",
     "lbm_nd_moments", "lbm_nd_populations", "lbm_nd_energy", "lbm_nd_step_count",
     "lbm_nd_destroy", "lbm_nd_last_error",
@@ -157,6 +157,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_residual_noalloc": (st, [vp, vp, vp, vp, vp, vp, ctypes.c_longlong,
                                       ctypes.c_double, c_long, vp, dp, dp]),
         "lbm_check_bounded_wait": (st, [vp, ctypes.POINTER(ctypes.c_int), dp]),
+        "lbm_probe_resident_wait": (st, [vp]),
         "lbm_nd_lattice_speed": (ctypes.c_double, [ctypes.c_int]),
         "lbm_nd_create": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
@@ -356,6 +357,12 @@ class Lattice:
 
     def sync(self):
         self._check(self._lib.lbm_sync(self._ctx))
+
+    def probe_resident_wait(self):
+        """lbm_probe_resident_wait: runs the cluster-resident kernel's bounded
+        ghost wait against a barrier nothing completes (about 2 s, async);
+        the next synchronising call raises LBMError(ETIMEOUT)."""
+        self._check(self._lib.lbm_probe_resident_wait(self._ctx))
 
     def moments(self, out=None):
         """(e, qx, qy) of the current state as numpy [ny, nx] float64.

@@ -799,6 +799,8 @@ lbm_status lbm_set_state(lbm_ctx *c, const void *host, size_t bytes) {
     for (int i = 0; i < 2; ++i)
         CK(c, cudaMemcpyAsync(c->buf[i], p + sizeof(h) + i * c->buf_bytes, c->buf_bytes,
                               cudaMemcpyHostToDevice, c->stream));
+    // a restored state starts with a clear status word (no earlier time-out)
+    if (c->aux) CK(c, cudaMemsetAsync(status_word(c), 0, sizeof(int), c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     drop_graphs(c);
     c->cur = h.cur;
@@ -1030,6 +1032,14 @@ lbm_status lbm_check_bounded_wait(void *stream, int *gave_up, double *seconds) {
     if (err != cudaSuccess) return cuda_fail(nullptr, err, "lbm_check_bounded_wait");
     if (gave_up) *gave_up = st != 0;
     if (seconds) *seconds = ms / 1e3;
+    return LBM_OK;
+}
+
+lbm_status lbm_probe_resident_wait(lbm_ctx *c) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    DeviceGuard g(c->device);
+    if (lbm_status s = ensure_scratch(c, false)) return s;
+    CK(c, launch_resident_wait_probe(status_word(c), c->stream));
     return LBM_OK;
 }
 

@@ -98,6 +98,9 @@ cudaError_t launch_resident(const float *src, float *out_last, float *out_prev, 
 // Runs the staged kernel's bounded mbarrier wait against a barrier nothing
 // completes (one CTA, ~2 s); the wait gives up and ORs 1 into *status.
 cudaError_t launch_wait_probe(int *status, cudaStream_t stream);
+// The same for the cluster-resident kernel's ghost wait (one-CTA cluster);
+// ORs 2 into *status.
+cudaError_t launch_resident_wait_probe(int *status, cudaStream_t stream);
 
 // Blocks of the stand-alone residual pass (sizes its per-block partials).
 long long readout_blocks(int precision, int nx, int ny, int bc_x, int bc_y);

@@ -29,6 +29,7 @@
 #include <algorithm>
 
 #include "lbm_kernels.h"
+#include "mbarrier.cuh"
 
 namespace plbm {
 namespace {
@@ -58,9 +59,6 @@ __device__ __forceinline__ float ld_cluster(uint32_t local_addr, unsigned rank) 
 // populations that leave its slab with an asynchronous remote store whose
 // completion counts bytes on an mbarrier of the receiving CTA; the receiver
 // waits for its bytes (bounded) before it next pulls from its ghosts.
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
 __device__ __forceinline__ uint32_t map_to(uint32_t local_addr, unsigned rank) {
     uint32_t remote;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
@@ -73,35 +71,10 @@ __device__ __forceinline__ void st_async(uint32_t remote_addr, float v, uint32_t
         "r"(__float_as_uint(v)), "r"(remote_bar)
         : "memory");
 }
-__device__ __forceinline__ void bar_init(uint64_t *bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void bar_expect(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool bar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait (iteration and clock limits, ~2 s): a wait that gives up
-// sets bit 2 of *status (read back as LBM_ETIMEOUT) and returns.
-__device__ __forceinline__ void bar_wait(uint64_t *bar, uint32_t parity, int *status) {
-    if (bar_try(bar, parity)) return;
-    const long long t0 = clock64();
-    for (long long it = 0; it < (1LL << 28); ++it) {
-        if (bar_try(bar, parity)) return;
-        if ((it & 255) == 255 && clock64() - t0 > 4000000000LL) break;
-    }
-    atomicOr(status, 2);
+// The bounded wait for a buffer's ghost bytes (about 2 s): false when it
+// gave up, after setting STATUS_RESIDENT in *status (LBM_ETIMEOUT).
+__device__ __forceinline__ bool ghost_wait(uint64_t *bar, uint32_t parity, int *status) {
+    return mbar_wait<true>(bar, parity, status, STATUS_RESIDENT);
 }
 
 // Slab geometry shared by every CTA of the cluster.  A slab is stored with
@@ -183,8 +156,8 @@ step_resident(const float *src, float *out_last, float *out_prev, long long plan
     };
 
     if (threadIdx.x == 0) {
-        bar_init(&full[0]);
-        bar_init(&full[1]);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int l = threadIdx.x; l < count; l += blockDim.x) {
@@ -267,6 +240,7 @@ step_resident(const float *src, float *out_last, float *out_prev, long long plan
         hi_bar1 = map_to(smem_u32(&full[1]), (unsigned)hi_owner);
     }
 
+    bool gave_up = false, aborted = false;
     for (long s = 0; s < steps; ++s) {
         const float *A = sm + (s & 1) * 8 * pb;
         float *B = sm + ((s & 1) ^ 1) * 8 * pb;
@@ -274,7 +248,7 @@ step_resident(const float *src, float *out_last, float *out_prev, long long plan
         // ghosts are exchanged for the steps that follow within this launch
         const bool more = s + 1 < steps;
         const uint32_t lo_bar = b ? lo_bar1 : lo_bar0, hi_bar = b ? hi_bar1 : hi_bar0;
-        if (exchange && more && threadIdx.x == 0) bar_expect(&full[b], ghost_bytes);
+        if (exchange && more && threadIdx.x == 0) mbar_expect_tx(&full[b], ghost_bytes);
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             if (nly[j] < 0) continue;
@@ -324,19 +298,27 @@ step_resident(const float *src, float *out_last, float *out_prev, long long plan
                 }
             }
         }
-        // this CTA's writes of step s before any of its threads reads them
-        __syncthreads();
+        // this CTA's writes of step s before any of its threads reads them;
+        // the same barrier tells every thread whether a wait of the step
+        // before gave up, so that all of them leave the loop together
+        if (__syncthreads_or(gave_up)) {
+            aborted = true;
+            break;
+        }
         // and the neighbours' ghosts of buffer b, the (s >> 1)-th use of its
         // barrier.  A neighbour writes these ghosts again only two steps
         // later, after it has received this CTA's edge nodes of step s + 1,
         // which are sent after they were pulled from the ghosts.
-        if (exchange && more) bar_wait(&full[b], (uint32_t)((s >> 1) & 1), status);
+        if (exchange && more) gave_up = !ghost_wait(&full[b], (uint32_t)((s >> 1) & 1), status);
     }
 
     // post-collision state of the last step (buffer steps & 1) and of the
-    // step before it (the other buffer)
+    // step before it (the other buffer).  After a wait gave up the state is
+    // not valid (the status word says so): nothing is written, no more
+    // ghosts are sent or awaited, and the CTA goes straight to the final
+    // barrier, so a stalled exchange costs one wait limit per launch.
     const int last = (int)(steps & 1);
-    for (int l = threadIdx.x; l < count; l += blockDim.x) {
+    for (int l = threadIdx.x; l < count && !aborted; l += blockDim.x) {
         const int ly = l / wx, lx = l - ly * wx;
         const long long node = (long long)(y0 + ly) * nx + (x0 + lx);
 #pragma unroll
@@ -469,6 +451,29 @@ cudaError_t resident_plan(int precision, int nx, int ny, int cluster_req, Reside
         return cudaSuccess;
     }
     return cudaErrorNotSupported;
+}
+
+namespace {
+
+// The resident kernel's ghost wait on a fresh barrier that nothing
+// completes, in one thread of a one-CTA cluster: the wait gives up at its
+// limit (about 2 s) and sets STATUS_RESIDENT in *status, exactly as a
+// stalled ghost exchange would.
+__global__ void __cluster_dims__(1, 1, 1) resident_wait_probe(int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ghost_wait(&bar, 0u, status);
+}
+
+}  // namespace
+
+cudaError_t launch_resident_wait_probe(int *status, cudaStream_t stream) {
+    resident_wait_probe<<<1, 32, 0, stream>>>(status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_resident(const float *src, float *out_last, float *out_prev, int nx, int ny,

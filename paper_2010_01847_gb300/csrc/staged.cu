@@ -24,56 +24,18 @@
 #include <type_traits>
 
 #include "lbm_kernels.h"
+#include "mbarrier.cuh"
 #include "pairs16.cuh"
 
 namespace plbm {
 
 namespace {
 
-constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
-constexpr long long WAIT_ITERS = 1LL << 28;
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return smem_u32(p); }
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status) {
-    if (mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (long long it = 0; it < WAIT_ITERS; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 255) == 255 && clock64() - t0 > WAIT_CYCLES) break;
-    }
-    atomicOr(status, 1);
-    return false;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
+// Bounded wait of this kernel (sets STATUS_STAGED when it gives up).
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity, int *status) {
+    return mbar_wait<false>(bar, parity, status, STATUS_STAGED);
 }
 
 // Global -> shared bulk copy completing on an mbarrier (the TMA engine).
@@ -182,7 +144,7 @@ step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long
                  tile += gridDim.x, ++kk) {
                 const int s = (int)(kk % stages);
                 const uint32_t ph = (uint32_t)((kk / stages) & 1);
-                if (!mbar_wait(&empty[s], ph ^ 1u, status)) break;
+                if (!stage_wait(&empty[s], ph ^ 1u, status)) break;
                 const int y = (int)(tile / tiles_per_row);
                 const int x0 = (int)(tile - (long long)y * tiles_per_row) * W;
                 mbar_expect_tx(&full[s], (uint32_t)SB);
@@ -207,7 +169,7 @@ step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long
             }
             // every copy issued must land before the CTA may exit
             for (long long kk = issued > stages ? issued - stages : 0; kk < issued; ++kk)
-                mbar_wait(&full[kk % stages], (uint32_t)((kk / stages) & 1), status);
+                stage_wait(&full[kk % stages], (uint32_t)((kk / stages) & 1), status);
         }
     } else {
         // ---------------- consumers ----------------
@@ -216,7 +178,7 @@ step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long
         for (long long tile = blockIdx.x, kk = 0; tile < n_tiles; tile += gridDim.x, ++kk) {
             const int s = (int)(kk % stages);
             const uint32_t ph = (uint32_t)((kk / stages) & 1);
-            if (!mbar_wait(&full[s], ph, status)) break;
+            if (!stage_wait(&full[s], ph, status)) break;
             const int y = (int)(tile / tiles_per_row);
             const int x0 = (int)(tile - (long long)y * tiles_per_row) * W;
             const T *stage = ring + (size_t)s * 8 * RL;
@@ -420,7 +382,7 @@ __global__ void wait_probe(int *status) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0) mbar_wait(&bar, 0u, status);
+    if (threadIdx.x == 0) stage_wait(&bar, 0u, status);
 }
 
 cudaError_t launch_wait_probe(int *status, cudaStream_t stream) {

@@ -201,18 +201,22 @@ def big_fields():
     return w, inputs.initial_fields(w)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
-def test_8192_sampled_nodes_light_cone(big_fields, precision):
+@pytest.mark.parametrize("precision,n,samples", [
+    ("fp32", 24, 32), ("fp16", 24, 32), ("bf16", 24, 32),
+    # 300 steps: FP32 rounding has accumulated over 300 launches of the
+    # bench configuration; (601)^2 oracle windows, 16 nodes
+    ("fp32", 300, 16)])
+def test_8192_sampled_nodes_light_cone(big_fields, precision, n, samples):
     """After n steps a node depends only on nodes within n cells, so the oracle
     on a periodic (2n+1)^2 window around a node gives its exact value."""
     w, (e, qx, qy) = big_fields
     tau_N, tau_R = tau_pair(w.kn_N, w.kn_R, w.length)
-    n = 24
     g = gpu_run(w.nx, w.ny, tau_N, tau_R, (e, qx, qy), n, precision=precision)
     ge, gqx, gqy = [t.cpu().numpy() for t in g.moments_device()]
+    g.close()
     rng = np.random.default_rng(1)
     pts = [(0, 0), (w.ny - 1, w.nx - 1), (0, w.nx - 1), (w.ny - 1, 0)] + \
-        [tuple(p) for p in rng.integers(0, w.nx, (28, 2))]
+        [tuple(p) for p in rng.integers(0, w.nx, (samples - 4, 2))]
     res = []
     for (y, x) in pts:
         win = [_window(a, y, x, n) for a in (e, qx, qy)]
