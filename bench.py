@@ -243,7 +243,8 @@ def measured_peak():
 # sources that define each stream-collide kernel
 KERNEL_SOURCES = {
     "step_vector": ["lbm_device.cuh", "pairs16.cuh", "vector_pull.cuh", "stream_collide.cu"],
-    "step_vector16": ["lbm_device.cuh", "pairs16.cuh", "vector_pull.cuh", "stream_collide.cu"],
+    "step_pipe16": ["lbm_device.cuh", "refs16.cuh", "pairs16.cuh", "vector_pull.cuh",
+                    "pipe16.cu"],
     "step_staged": ["lbm_device.cuh", "pairs16.cuh", "staged.cu"],
     "step_scalar": ["lbm_device.cuh", "pairs16.cuh", "stream_collide.cu"],
 }
@@ -410,14 +411,15 @@ def run_native(args):
     sites = nx * ny
     value = job_value(world, sites, args.steps, elapsed)
 
-    # roofline of the stream-collide kernel
-    bps = 16 * STORAGE_BYTES[args.precision]
+    # roofline of the stream-collide kernel: one state buffer read and one
+    # written per site (16-bit storage includes the tiles' references)
+    bps = lat.bytes_per_site_update
     avg_launch = kern_s / kern_steps
     achieved = bps * sites / avg_launch / 1e9
     peak, peak_kind = measured_peak()
     kname = "step_" + lat.kernel
     if lat.kernel == "vector" and STORAGE_BYTES[args.precision] == 2:
-        kname = "step_vector16"             # plain 16-bit steps: the node-pair kernel
+        kname = "step_pipe16"               # plain 16-bit steps: the pipelined node-pair kernel
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": ncu_traffic(kname, args.precision, nx, ny),
             "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else 'profiling-recipe fallback 6.8 TB/s'})",

@@ -464,9 +464,12 @@ class Lattice:
         self._check(self._lib.lbm_set_graph_chunk(self._ctx, int(steps)))
 
     @property
-    def bytes_per_site_update(self) -> int:
-        """Algorithmic bytes per site update: 8 populations read + 8 written."""
-        return 16 * _ELEM[self.precision]
+    def bytes_per_site_update(self) -> float:
+        """Algorithmic bytes per site update: one state buffer read and one
+        written per node, i.e. 8 populations each way and, with 16-bit
+        storage, the node's share of its tile's references."""
+        nbytes = self._lib.lbm_population_bytes(Grid(self.nx, self.ny), self.precision)
+        return 2.0 * nbytes / (self.nx * self.ny)
 
 
 class Batch:

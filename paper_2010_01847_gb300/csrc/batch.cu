@@ -4,8 +4,9 @@
 //
 // Layout: the instances' population planes are packed one after another in
 // two shared buffers (instance i: 8 planes of nx_i * ny_i elements starting
-// at element off_i); residual histories likewise (3 planes of the compute
-// type per instance).  Work is cut into items of `tpi` threads x V nodes of
+// at element off_i, then, with 16-bit storage, its plane of tile references,
+// refs16.cuh); residual histories likewise (3 planes of the compute type per
+// instance).  Work is cut into items of `tpi` threads x V nodes of
 // one instance; a persistent grid walks the list of items of the instances
 // still running.  Each item runs the same vectorised pull, boundary and
 // collision as the single-lattice vector kernel (Eqs. 13, 15, 16, 53-54, 58,
@@ -88,8 +89,9 @@ batch_kernel(const T *__restrict__ src, T *__restrict__ dst,
         const InstDev<C> I = inst[item.inst];
         const long long t = (long long)item.first + threadIdx.x;
         C d[8][V];
+        uint2 enc = make_uint2(0u, 0u);   // 16-bit storage: the tile's next reference
         const VecPos p = vector_pull<T>(src + I.off, I.nx, I.ny, I.plane, I.bc_x, I.bc_y, I.k, t,
-                                        d);
+                                        d, &enc);
         C loc[5] = {C(0), C(0), C(0), C(0), C(0)};
         if (p.active) {
             const long long out = (long long)p.y * I.nx + p.x0;
@@ -105,16 +107,20 @@ batch_kernel(const T *__restrict__ src, T *__restrict__ dst,
                 residual_vec<C, V>(n, I.k, inv_s, hist + I.hoff, I.plane, out, have_prev != 0,
                                    loc);
             if (MODE != B_RES_ONLY) {
-#pragma unroll
-                for (int j = 0; j < V; ++j) {
-                    collide(n[j], I.k);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) d[i][j] = n[j][i];
-                }
                 T *o = dst + I.off;
+                if constexpr (sizeof(T) == 2) {
+                    collide_store16<T>(n, I.k, o, I.plane, out, t, enc);   // tile t = vector t
+                } else {
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    st_stream(o + (long long)i * I.plane + out, Pack<T>::pack(d[i]));
+                    for (int j = 0; j < V; ++j) {
+                        collide(n[j], I.k);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) d[i][j] = n[j][i];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        st_stream(o + (long long)i * I.plane + out, Pack<T>::pack(d[i]));
+                }
             }
         }
         if (MODE != B_STEP) {
@@ -321,7 +327,7 @@ Params params_of(const lbm_instance &in) {
 }
 
 template <typename C>
-Coef<C> coef_of(const lbm_instance &in, double scale) {
+Coef<C> coef_of(const lbm_instance &in, double scale, int precision) {
     const Params p = params_of(in);
     Coef<C> k{};
     k.omega = (C)(1.0 / p.tau);
@@ -335,6 +341,7 @@ Coef<C> coef_of(const lbm_instance &in, double scale) {
     k.u_diag = ((C)1 - k.u_axis) / (C)2;
     k.jump_axis = (C)(scale * (2.0 / 9.0) * in.bc.delta_e);
     k.jump_diag = (C)(scale * (1.0 / 36.0) * in.bc.delta_e);
+    set_tile_refs(k, precision, in.nx, in.ny, p.tau, p.tau_r);
     return k;
 }
 
@@ -353,7 +360,7 @@ cudaError_t upload_table(lbm_batch *b) {
         t[i].ny = in.ny;
         t[i].bc_x = in.bc.x;
         t[i].bc_y = in.bc.y;
-        t[i].k = coef_of<C>(in, b->scale);
+        t[i].k = coef_of<C>(in, b->scale, b->precision);
     }
     cudaError_t e = cudaMemcpyAsync(b->dinst, t.data(), sizeof(InstDev<C>) * b->count,
                                     cudaMemcpyHostToDevice, b->stream);
@@ -529,7 +536,7 @@ lbm_status lbm_batch_create(const lbm_instance *inst, int count, lbm_precision p
         const long long n = (long long)inst[i].nx * inst[i].ny;
         b->off[i] = b->total;
         b->hoff[i] = b->htotal;
-        b->total += 8 * n;
+        b->total += state_elems(precision, inst[i].nx, inst[i].ny);
         b->htotal += 3 * n;
         b->max_plane = std::max(b->max_plane, n);
         b->max_items += (n / V + 127) / 128;     // items of at least 128 threads
@@ -642,27 +649,27 @@ lbm_status lbm_batch_init(lbm_batch *b, const double *e, const double *qx, const
         switch (b->precision) {
             case PREC_FP32:
                 err = launch_init<float>(de, qx ? dqx : nullptr, qy ? dqy : nullptr, in.nx, in.ny,
-                                         b->e_ref, b->scale, coef_of<float>(in, b->scale),
+                                         b->e_ref, b->scale, coef_of<float>(in, b->scale, b->precision),
                                          (float *)b->buf[1] + o, (float *)b->buf[0] + o,
                                          b->stream);
                 break;
             case PREC_FP64:
                 err = launch_init<double>(de, qx ? dqx : nullptr, qy ? dqy : nullptr, in.nx,
                                           in.ny, b->e_ref, b->scale,
-                                          coef_of<double>(in, b->scale),
+                                          coef_of<double>(in, b->scale, b->precision),
                                           (double *)b->buf[1] + o, (double *)b->buf[0] + o,
                                           b->stream);
                 break;
             case PREC_FP16:
                 err = launch_init<__half>(de, qx ? dqx : nullptr, qy ? dqy : nullptr, in.nx,
                                           in.ny, b->e_ref, b->scale,
-                                          coef_of<float>(in, b->scale), (__half *)b->buf[1] + o,
+                                          coef_of<float>(in, b->scale, b->precision), (__half *)b->buf[1] + o,
                                           (__half *)b->buf[0] + o, b->stream);
                 break;
             default:
                 err = launch_init<__nv_bfloat16>(
                     de, qx ? dqx : nullptr, qy ? dqy : nullptr, in.nx, in.ny, b->e_ref, b->scale,
-                    coef_of<float>(in, b->scale), (__nv_bfloat16 *)b->buf[1] + o,
+                    coef_of<float>(in, b->scale, b->precision), (__nv_bfloat16 *)b->buf[1] + o,
                     (__nv_bfloat16 *)b->buf[0] + o, b->stream);
         }
         if (err != cudaSuccess) return bcuda(b, err, "batch init kernel");
@@ -845,22 +852,22 @@ lbm_status lbm_batch_moments(lbm_batch *b, int i, double *e, double *qx, double 
     switch (b->precision) {
         case PREC_FP32:
             err = launch_moments<float>((const float *)b->buf[src] + o, rd,
-                                        coef_of<float>(in, b->scale), d[0], d[1], d[2],
+                                        coef_of<float>(in, b->scale, b->precision), d[0], d[1], d[2],
                                         b->stream);
             break;
         case PREC_FP64:
             err = launch_moments<double>((const double *)b->buf[src] + o, rd,
-                                         coef_of<double>(in, b->scale), d[0], d[1], d[2],
+                                         coef_of<double>(in, b->scale, b->precision), d[0], d[1], d[2],
                                          b->stream);
             break;
         case PREC_FP16:
             err = launch_moments<__half>((const __half *)b->buf[src] + o, rd,
-                                         coef_of<float>(in, b->scale), d[0], d[1], d[2],
+                                         coef_of<float>(in, b->scale, b->precision), d[0], d[1], d[2],
                                          b->stream);
             break;
         default:
             err = launch_moments<__nv_bfloat16>((const __nv_bfloat16 *)b->buf[src] + o, rd,
-                                                coef_of<float>(in, b->scale), d[0], d[1], d[2],
+                                                coef_of<float>(in, b->scale, b->precision), d[0], d[1], d[2],
                                                 b->stream);
     }
     if (err != cudaSuccess) return bcuda(b, err, "batch moments");
@@ -1024,22 +1031,22 @@ lbm_status lbm_batch_profiles(lbm_batch *b, float *out) {
         switch (b->precision) {
             case PREC_FP32:
                 err = launch_moments<float>((const float *)b->buf[src] + o, rd,
-                                            coef_of<float>(in, b->scale), d[0], d[1], nullptr,
+                                            coef_of<float>(in, b->scale, b->precision), d[0], d[1], nullptr,
                                             b->stream);
                 break;
             case PREC_FP64:
                 err = launch_moments<double>((const double *)b->buf[src] + o, rd,
-                                             coef_of<double>(in, b->scale), d[0], d[1], nullptr,
+                                             coef_of<double>(in, b->scale, b->precision), d[0], d[1], nullptr,
                                              b->stream);
                 break;
             case PREC_FP16:
                 err = launch_moments<__half>((const __half *)b->buf[src] + o, rd,
-                                             coef_of<float>(in, b->scale), d[0], d[1], nullptr,
+                                             coef_of<float>(in, b->scale, b->precision), d[0], d[1], nullptr,
                                              b->stream);
                 break;
             default:
                 err = launch_moments<__nv_bfloat16>((const __nv_bfloat16 *)b->buf[src] + o, rd,
-                                                    coef_of<float>(in, b->scale), d[0], d[1],
+                                                    coef_of<float>(in, b->scale, b->precision), d[0], d[1],
                                                     nullptr, b->stream);
         }
         if (err != cudaSuccess) return bcuda(b, err, "batch profile moments");
@@ -1083,11 +1090,11 @@ lbm_status lbm_batch_init_profiles(lbm_batch *b, const float *profiles) {
         cudaError_t err;
         if (b->precision == PREC_FP32)
             err = launch_init<float>(de, dqx, dqy, in.nx, in.ny, b->e_ref, 1.0,
-                                     coef_of<float>(in, 1.0), (float *)b->buf[1] + o,
+                                     coef_of<float>(in, 1.0, b->precision), (float *)b->buf[1] + o,
                                      (float *)b->buf[0] + o, b->stream);
         else
             err = launch_init<double>(de, dqx, dqy, in.nx, in.ny, b->e_ref, 1.0,
-                                      coef_of<double>(in, 1.0), (double *)b->buf[1] + o,
+                                      coef_of<double>(in, 1.0, b->precision), (double *)b->buf[1] + o,
                                       (double *)b->buf[0] + o, b->stream);
         if (err != cudaSuccess) return bcuda(b, err, "batch profile init");
     }

@@ -137,6 +137,7 @@ Coef<C> make_coef(const lbm_ctx *c) {
                                                           : 0.0);
         k.side_flux[sd] = (C)(kind == LBM_SIDE_HEAT_FLUX ? c->scale * v / c->kappa : 0.0);
     }
+    set_tile_refs(k, c->precision, c->nx, c->ny, c->tau, c->tau_r);
     return k;
 }
 
@@ -343,6 +344,10 @@ bool resident_ok(lbm_ctx *c) {
 
 int resolve_kernel(lbm_ctx *c, int requested) {
     const bool vec_ok = c->nx % vector_width(c->precision) == 0;
+    // plain 16-bit steps on the vector layout run the pipelined kernel, set
+    // up here, outside any stream capture
+    if (vec_ok && has_tile_refs(c->precision) && prepare_pipe16(c->precision) != cudaSuccess)
+        (void)cudaGetLastError();
     // without timing: small FP32 lattices run cluster-resident, n steps per
     // launch (measured 1.5-2.4x faster than one launch per step up to 16384
     // nodes; beyond that 16 SMs do less than the whole GPU)
@@ -551,7 +556,7 @@ double lbm_tau_from_kn(double kn, double length) { return kn * length * std::sqr
 
 size_t lbm_population_bytes(lbm_grid grid, lbm_precision precision) {
     if (grid.nx < 1 || grid.ny < 1 || precision < LBM_FP32 || precision > LBM_FP64) return 0;
-    return (size_t)8 * (size_t)grid.nx * (size_t)grid.ny * elem_size(precision);
+    return (size_t)state_elems(precision, grid.nx, grid.ny) * elem_size(precision);
 }
 
 lbm_status lbm_create(lbm_grid grid, double tau_N, double tau_R, lbm_boundary bc,

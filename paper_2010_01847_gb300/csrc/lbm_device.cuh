@@ -49,6 +49,15 @@ struct Coef {
     C side_axis[4];           // isothermal: s w_i (e_s - e_ref), Eq. 55
     C side_diag[4];
     C side_flux[4];           // heat flux: s q_0 (2 tau_r + 1)/(2 tau_r), Eq. 57
+    // 16-bit storage only (refs16.cuh): populations are stored relative to a
+    // reference equilibrium of their tile of 2^tile_shift nodes of a row.
+    int tile_shift;           // 3: tiles of 8 nodes; 0: of one node; -1: no references
+    int tiles_x;              // tiles per row, nx >> tile_shift
+    long long ref_off;        // element offset of the reference plane, 8 nx ny
+    C rw_axis, rw_diag;       // 4 w_i, 4 h_i: reference populations from {rho, j} / 4
+    C rh_axis, rh_diag;
+    C ref_rho;                // 1 / (4 nodes-per-tile): tile sum of rho -> reference
+    C ref_gamma;              // gamma / (4 nodes-per-tile), gamma m = post-collision flux
 };
 
 // Storage traits: how a population plane element is stored and converted.
@@ -135,18 +144,20 @@ __device__ __forceinline__ V relax_minus(V d, V w, V neg_rho, V t, V neg_omega, 
     return f_fma(sigma, t, f_fma(neg_omega, f_add(d, neg_eq), d));
 }
 
-// The collision above in FP32 on one node (V = float) or on two nodes at once
-// (V = float2: lane x one node, lane y the other).  Operation order chosen
-// for accuracy: over 5000 steps of the 4096 x 4 second-sound pulse
-// (Kn_R = 0.1) the max error against FP64 is 7e-6 with eq in one rounding,
-// 1.2e-5 with w rho rounded separately.
+// The moments of Eqs. 53-54 before the kappa factor: rho = sum d_i and
+// m = sum c_i d_i, in the order every FP32 kernel forms them.
 template <typename V>
-__device__ __forceinline__ void collide_f32(V (&d)[8], const Coef<float> &k) {
-    const V rho = f_add(f_add(f_add(d[0], d[2]), f_add(d[1], d[3])),
-                        f_add(f_add(d[4], d[6]), f_add(d[5], d[7])));
+__device__ __forceinline__ void moments_f32(const V (&d)[8], V &rho, V &mx, V &my) {
+    rho = f_add(f_add(f_add(d[0], d[2]), f_add(d[1], d[3])),
+                f_add(f_add(d[4], d[6]), f_add(d[5], d[7])));
     const V s46 = f_sub(d[4], d[6]);
-    const V mx = f_add(f_add(f_sub(d[0], d[2]), s46), f_sub(d[7], d[5]));
-    const V my = f_add(f_add(f_sub(d[1], d[3]), s46), f_sub(d[5], d[7]));
+    mx = f_add(f_add(f_sub(d[0], d[2]), s46), f_sub(d[7], d[5]));
+    my = f_add(f_add(f_sub(d[1], d[3]), s46), f_sub(d[5], d[7]));
+}
+
+// The relaxation of collide_f32 given the node's moments.
+template <typename V>
+__device__ __forceinline__ void relax_f32(V (&d)[8], V rho, V mx, V my, const Coef<float> &k) {
     const V neg_lambda = splat<V>(-k.lambda);
     const V qx = f_fma(neg_lambda, mx, mx);             // q = m - lambda m
     const V qy = f_fma(neg_lambda, my, my);
@@ -167,6 +178,18 @@ __device__ __forceinline__ void collide_f32(V (&d)[8], const Coef<float> &k) {
     d[5] = relax_minus(d[5], wd, neg_rho, tm, no, sg);
     d[6] = relax_minus(d[6], wd, neg_rho, tp, no, sg);
     d[7] = relax_plus(d[7], wd, rho, tm, no, ns);
+}
+
+// The collision above in FP32 on one node (V = float) or on two nodes at once
+// (V = float2: lane x one node, lane y the other).  Operation order chosen
+// for accuracy: over 5000 steps of the 4096 x 4 second-sound pulse
+// (Kn_R = 0.1) the max error against FP64 is 7e-6 with eq in one rounding,
+// 1.2e-5 with w rho rounded separately.
+template <typename V>
+__device__ __forceinline__ void collide_f32(V (&d)[8], const Coef<float> &k) {
+    V rho, mx, my;
+    moments_f32(d, rho, mx, my);
+    relax_f32(d, rho, mx, my, k);
 }
 
 // FP32 compute (FP32 and 16-bit storage): the spelled-out form.
@@ -299,18 +322,6 @@ __device__ __forceinline__ void pull_node_with(const Load &load, int nx, int ny,
     if (sides_x || sides_y)
         apply_sides(d, k, sides_x && x == 0, sides_x && x == nx - 1, sides_y && y == 0,
                     sides_y && y == ny - 1);
-}
-
-template <typename T>
-__device__ __forceinline__ void pull_node(const T *__restrict__ src, long long plane,
-                                          int nx, int ny, int x, int y, int bc_x,
-                                          int bc_y, const Coef<typename Store<T>::C> &k,
-                                          typename Store<T>::C (&d)[8]) {
-    pull_node_with(
-        [&](int i, int sx, int sy) {
-            return Store<T>::load(src[(long long)i * plane + (long long)sy * nx + sx]);
-        },
-        nx, ny, x, y, bc_x, bc_y, k, d);
 }
 
 // Residual contribution of one node of the state at step n (pulled, after

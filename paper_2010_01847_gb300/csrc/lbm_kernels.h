@@ -21,6 +21,47 @@ enum { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2, PREC_FP64 = 3 };
 enum { KERNEL_AUTO = 0, KERNEL_SCALAR = 1, KERNEL_VECTOR = 2, KERNEL_STAGED = 3,
        KERNEL_RESIDENT = 4 };
 
+// 16-bit storage keeps a plane of tile references after the 8 population
+// planes (refs16.cuh): tiles of 8 nodes when nx is a multiple of 8, else of
+// one node.  tile_shift_of: 3 or 0 for 16-bit storage, -1 for the others.
+inline bool has_tile_refs(int precision) {
+    return precision == PREC_FP16 || precision == PREC_BF16;
+}
+inline int tile_shift_of(int precision, int nx) {
+    return !has_tile_refs(precision) ? -1 : (nx % 8 == 0 ? 3 : 0);
+}
+// Elements of the storage type in one state buffer of an nx x ny lattice.
+inline long long state_elems(int precision, int nx, int ny) {
+    const long long plane = (long long)nx * ny;
+    const int sh = tile_shift_of(precision, nx);
+    return 8 * plane + (sh < 0 ? 0 : 8 * (plane >> sh));
+}
+// The tile-reference fields of the coefficients (after the weights are set):
+// the reference populations R_i = 4 w_i rho~ + 4 h_i c_i . j~ of a stored
+// {rho, j} / 4, the tile-sum factors 1 / (4 nodes-per-tile) for rho and
+// gamma / (4 nodes-per-tile) for the flux, gamma = 1 - omega lambda -
+// sigma (1 - lambda) the factor the collision applies to m = sum c_i d_i
+// (Eqs. 15, 16 and 54 summed against c_i).
+template <typename C>
+inline void set_tile_refs(Coef<C> &k, int precision, int nx, int ny, double tau, double tau_r) {
+    k.tile_shift = tile_shift_of(precision, nx);
+    if (k.tile_shift < 0) return;
+    k.tiles_x = nx >> k.tile_shift;
+    k.ref_off = 8LL * nx * ny;
+    k.rw_axis = (C)4 * k.w_axis;
+    k.rw_diag = (C)4 * k.w_diag;
+    k.rh_axis = (C)4 * k.h_axis;
+    k.rh_diag = (C)4 * k.h_diag;
+    const double per_tile = 4.0 * (double)(1 << k.tile_shift);
+    const double omega = 1.0 / tau;
+    const bool resistive = tau_r < 1e300;
+    const double lambda = resistive ? 1.0 / (2.0 * tau_r + 1.0) : 0.0;
+    const double sigma = resistive ? (1.0 - 1.0 / (2.0 * tau)) / tau_r : 0.0;
+    const double gamma = 1.0 - omega * lambda - sigma * (1.0 - lambda);
+    k.ref_rho = (C)(1.0 / per_tile);
+    k.ref_gamma = (C)(gamma / per_tile);
+}
+
 // Sets the text lbm_last_error(NULL) returns.
 void set_global_error(const char *msg);
 
@@ -53,6 +94,15 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
                         const Coef<typename Store<T>::C> &k, int *status,
                         const ResidualReq<typename Store<T>::C> *rq, const StagedPlan &plan,
                         int *blocks_out, cudaStream_t stream);
+
+// Plain steps of 16-bit storage on the vector layout (pipe16.cu): a
+// persistent kernel; prepare_pipe16 sets it up on the current device
+// (launch attributes, grid size; call outside stream capture), the launch
+// returns cudaErrorNotReady without it.
+cudaError_t prepare_pipe16(int precision);
+template <typename T>
+cudaError_t launch_step_pipe16(const T *src, T *dst, int nx, int ny, int bc_x, int bc_y,
+                               const Coef<float> &k, cudaStream_t stream);
 
 // Largest number of blocks a step launch of this kernel can have (sizes the
 // per-block residual partials).

@@ -6,12 +6,12 @@
 // shift of those words by one 16-bit value, and each word converts to a
 // float2 that is a node pair of one population, which the packed FP32 pair
 // instructions collide at once (collide_f32<float2>: the same bits as the
-// node-by-node collision).  The vector kernel and the staged kernel use this
-// for 16-bit storage; inputs stay packed until their pair is collided, which
-// keeps fewer values live than unpacking all 8 nodes first.
+// node-by-node collision).  The vector kernels use this for 16-bit storage;
+// inputs stay packed until their pair is collided, which keeps fewer values
+// live than unpacking all 8 nodes first.
 #pragma once
 
-#include "lbm_device.cuh"
+#include "refs16.cuh"
 
 namespace plbm {
 
@@ -43,33 +43,6 @@ __device__ __forceinline__ void set_word(uint4 &v, int m, unsigned r) {
     else v.w = r;
 }
 
-// A word's two 16-bit values as a float2 (low half -> x; exact) and back
-// (x -> low half, rounded to nearest even, as Store<T>::put), in registers.
-template <typename T> __device__ __forceinline__ float2 word_to_f2(unsigned w);
-template <> __device__ __forceinline__ float2 word_to_f2<__half>(unsigned w) {
-    float a, b;
-    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
-        "cvt.f32.f16 %0, lo;\n\tcvt.f32.f16 %1, hi;\n\t}"
-        : "=f"(a), "=f"(b)
-        : "r"(w));
-    return make_float2(a, b);
-}
-template <> __device__ __forceinline__ float2 word_to_f2<__nv_bfloat16>(unsigned w) {
-    // a bfloat16 is the high half of the float with the same value
-    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-}
-template <typename T> __device__ __forceinline__ unsigned f2_to_word(float2 v);
-template <> __device__ __forceinline__ unsigned f2_to_word<__half>(float2 v) {
-    unsigned r;
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(v.y), "f"(v.x));
-    return r;
-}
-template <> __device__ __forceinline__ unsigned f2_to_word<__nv_bfloat16>(float2 v) {
-    unsigned r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(v.y), "f"(v.x));
-    return r;
-}
-
 // Seam jumps (Eqs. 59-60) on the edge nodes of a thread's 8, in FP32 after
 // conversion, as the node-by-node kernels add them: with `left`, node 0 of
 // every c_x = +1 population gets + (the jump if `left_jump`, else 0); with
@@ -86,17 +59,33 @@ struct NoPairHook {
 
 // Walls (Eq. 58 on the bottom / top row), collision, and repacking of the 8
 // nodes held in w (after the shift), in place: word m of w[i] becomes the
-// post-collision values of nodes 2m, 2m + 1 of population i.  hook(m, f)
-// sees each pair's pulled state (after the walls, before the collision).
+// post-collision values of nodes 2m, 2m + 1 of population i.  With storage
+// relative to tile references (refs16.cuh) every pulled value of plane i
+// first gets Rd[i] added (the reference population of the tile it was
+// pulled from), except the node shifted in from the neighbouring tile of a
+// c_x = +1 (node 0) or c_x = -1 (node 7) plane, which gets Rx[i]; the
+// post-collision values are stored less Re[i] (the reference of this tile
+// for the next step's readers), and the tile's sums of rho, m_x, m_y
+// (moments_f32, tree order of tile_tree_pairs) come back in sums.
+// hook(m, f) sees each pair's pulled state (after the walls, before the
+// collision).
 template <typename T, typename Hook = NoPairHook>
 __device__ __forceinline__ void collide_words16(uint4 (&w)[8], const Coef<float> &k,
                                                 const SeamAdd &seam, bool bottom, bool top,
+                                                const float (&Rd)[8], const float (&Rx)[8],
+                                                const float (&Re)[8], float (&sums)[3],
                                                 const Hook &hook = Hook()) {
+    float2 r01, x01, y01, r23, x23, y23;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         float2 f[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) f[i] = word_to_f2<T>(word_of(w[i], m));
+        for (int i = 0; i < 8; ++i) {
+            float2 R = make_float2(Rd[i], Rd[i]);
+            if (m == 0 && cx_of(i) > 0) R.x = Rx[i];
+            if (m == 3 && cx_of(i) < 0) R.y = Rx[i];
+            f[i] = f_add(word_to_f2<T>(word_of(w[i], m)), R);
+        }
         if (m == 0 && seam.left) {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
@@ -114,10 +103,20 @@ __device__ __forceinline__ void collide_words16(uint4 (&w)[8], const Coef<float>
         if (bottom) wall_bottom(f, k);
         if (top) wall_top(f, k);
         hook(m, f);
-        collide_f32<float2>(f, k);
+        float2 rho, mx, my;
+        moments_f32(f, rho, mx, my);
+        if (m == 0) { r01 = rho; x01 = mx; y01 = my; }
+        if (m == 1) { r01 = f_add(r01, rho); x01 = f_add(x01, mx); y01 = f_add(y01, my); }
+        if (m == 2) { r23 = rho; x23 = mx; y23 = my; }
+        if (m == 3) { r23 = f_add(r23, rho); x23 = f_add(x23, mx); y23 = f_add(y23, my); }
+        relax_f32(f, rho, mx, my, k);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) set_word(w[i], m, f2_to_word<T>(f[i]));
+        for (int i = 0; i < 8; ++i)
+            set_word(w[i], m, f2_to_word<T>(f_sub(f[i], make_float2(Re[i], Re[i]))));
     }
+    sums[0] = tile_tree_pairs(r01, r23);
+    sums[1] = tile_tree_pairs(x01, x23);
+    sums[2] = tile_tree_pairs(y01, y23);
 }
 
 }  // namespace plbm

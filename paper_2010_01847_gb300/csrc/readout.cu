@@ -21,6 +21,12 @@ __device__ __forceinline__ void state_node(const T *__restrict__ src, const Read
         const long long node = (long long)y * r.nx + x;
 #pragma unroll
         for (int i = 0; i < 8; ++i) d[i] = Store<T>::load(src[(long long)i * plane + node]);
+        if constexpr (sizeof(T) == 2) {        // stored relative to the node's tile reference
+            float R[8];
+            ref_pops(ref_of<T>(ld_ref_stored(src, k, tile_of(k, x, y))), k, R);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) d[i] = f_add(d[i], R[i]);
+        }
     }
 }
 
@@ -101,7 +107,7 @@ readout_vector(const T *__restrict__ src, Readout r, Coef<typename Store<T>::C> 
     const C inv_s = (C)r.inv_scale;
     C d[8][V];
     const VecPos p = r.pulled ? vector_pull<T>(src, r.nx, r.ny, plane, r.bc_x, r.bc_y, k, t, d)
-                              : vector_local<T>(src, r.nx, r.ny, plane, t, d);
+                              : vector_local<T>(src, r.nx, r.ny, plane, t, k, d);
     C loc[5] = {C(0), C(0), C(0), C(0), C(0)};
     if (p.active) {
         const long long out = (long long)p.y * r.nx + p.x0;
@@ -215,6 +221,77 @@ __global__ void init_kernel(const double *__restrict__ e, const double *__restri
     }
 }
 
+// The same for 16-bit storage, stored relative to tile references
+// (refs16.cuh): the step-0 state is stored against the reference of its
+// own moments, its collision against the reference of the collided state's
+// moments (there is no earlier step whose reference could be used), and
+// both buffers' tiles get {that reference, that reference}.  Every lane of a
+// warp runs each node (tile sums over aligned lanes); lanes past the end
+// work on the last node and store nothing.
+template <typename T>
+__global__ void init_kernel16(const double *__restrict__ e, const double *__restrict__ qx,
+                              const double *__restrict__ qy, int nx, int ny, double e_ref,
+                              double scale, Coef<float> k, T *__restrict__ pre,
+                              T *__restrict__ post) {
+    const long long n = (long long)nx * ny;
+    const float s = (float)scale;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const bool tiles8 = k.tile_shift == 3;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const long long at = base + (threadIdx.x & 31);
+        const bool valid = at < n;
+        const long long node = valid ? at : n - 1;
+        const int y = int(node / nx), x = int(node - (long long)y * nx);
+        const bool lead = valid && (x & ((1 << k.tile_shift) - 1)) == 0;
+        const long long tile = tile_of(k, x, y);
+        const float de = (float)(e[node] - e_ref);
+        const float a = qx ? (float)qx[node] : 0.f;
+        const float b = qy ? (float)qy[node] : 0.f;
+        const float wa = k.w_axis * de, wd = k.w_diag * de;
+        const float ta = k.h_axis * a, tb = k.h_axis * b;
+        const float tp = k.h_diag * (a + b), tm = k.h_diag * (a - b);
+        const float dv[8] = {wa + ta, wa + tb, wa - ta, wa - tb, wd + tp, wd - tm, wd - tp, wd + tm};
+        float d[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) d[i] = dv[i] * s;
+        float rho, mx, my;
+        moments_f32(d, rho, mx, my);
+        if (tiles8) {
+            rho = tile_tree_lanes(rho);
+            mx = tile_tree_lanes(mx);
+            my = tile_tree_lanes(my);
+        }
+        // a state before collision: its reference flux is its own first moment
+        const uint2 rpre = next_ref<T>(rho, mx, my, k, k.ref_rho);
+        float R[8];
+        ref_pops(ref_of<T>(rpre), k, R);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const T v = Store<T>::put(f_sub(d[i], R[i]));
+            if (valid) pre[(long long)i * n + node] = v;
+            d[i] = f_add(Store<T>::load(v), R[i]);        // the state as the read-outs see it
+        }
+        if (lead) st_ref(pre, k, tile, rpre, rpre);
+        moments_f32(d, rho, mx, my);
+        float sr = rho, sx = mx, sy = my;
+        if (tiles8) {
+            sr = tile_tree_lanes(sr);
+            sx = tile_tree_lanes(sx);
+            sy = tile_tree_lanes(sy);
+        }
+        relax_f32(d, rho, mx, my, k);
+        const uint2 rpost = next_ref<T>(sr, sx, sy, k, k.ref_gamma);
+        ref_pops(ref_of<T>(rpost), k, R);
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                post[(long long)i * n + node] = Store<T>::put(f_sub(d[i], R[i]));
+        }
+        if (lead) st_ref(post, k, tile, rpost, rpost);
+    }
+}
+
 // Largest per-node bound (2/9)|e - e_ref| + (1/3)(|qx| + |qy|) >= max |d_i|
 // (unscaled), in FP32, maxed per warp; non-finite input -> +inf.
 __global__ void max_deviation_kernel(const double *__restrict__ e, const double *__restrict__ qx,
@@ -324,9 +401,12 @@ template <typename T>
 cudaError_t launch_init(const double *e, const double *qx, const double *qy, int nx, int ny,
                         double e_ref, double scale, const Coef<typename Store<T>::C> &k, T *pre,
                         T *post, cudaStream_t stream) {
-    init_kernel<T><<<grid_for((long long)nx * ny, 256), 256, 0, stream>>>(e, qx, qy, nx, ny,
-                                                                        e_ref, scale, k, pre,
-                                                                        post);
+    if constexpr (sizeof(T) == 2)
+        init_kernel16<T><<<grid_for((long long)nx * ny, 256), 256, 0, stream>>>(
+            e, qx, qy, nx, ny, e_ref, scale, k, pre, post);
+    else
+        init_kernel<T><<<grid_for((long long)nx * ny, 256), 256, 0, stream>>>(
+            e, qx, qy, nx, ny, e_ref, scale, k, pre, post);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,6 @@
 
 #include "lbm_kernels.h"
 #include "mbarrier.cuh"
-#include "pairs16.cuh"
 
 namespace plbm {
 
@@ -92,9 +91,6 @@ template <> struct Vec16<double> {
                           (unsigned)__double2loint(o[1]), (unsigned)__double2hiint(o[1]));
     }
 };
-// 16-bit storage: the consumers keep the 16-byte vectors packed (pairs16.cuh)
-template <> struct Vec16<__half> { static constexpr int V = 8; };
-template <> struct Vec16<__nv_bfloat16> { static constexpr int V = 8; };
 
 template <typename T, int CW> constexpr int tile_width() { return CW * 32 * Vec16<T>::V; }
 template <typename T, int CW> constexpr int row_len() {
@@ -104,10 +100,8 @@ template <typename T, int CW> constexpr int stage_bytes() {
     return 8 * row_len<T, CW>() * (int)sizeof(T);
 }
 
-// 16-bit storage keeps 8 nodes per consumer thread; asking for two CTAs per
-// SM caps its registers so two rings fit on an SM.
 template <typename T, int CW>
-__global__ void __launch_bounds__((CW + 1) * 32, (sizeof(T) == 2 ? 2 : 1))
+__global__ void __launch_bounds__((CW + 1) * 32, 1)
 step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long long plane,
             int bc_x, int bc_y, int stages, int hinted, Coef<typename Store<T>::C> k,
             int *status) {
@@ -185,28 +179,7 @@ step_staged(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long
             const bool bottom = walls && y == 0;
             const bool top = walls && y == ny - 1;
             const long long out = (long long)y * nx + x0 + t * V;
-            if constexpr (sizeof(T) == 2) {
-                // 16-bit storage: shift the packed words, collide node pairs
-                // (pairs16.cuh)
-                uint4 w[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const T *r = stage + i * RL + V + t * V;
-                    const unsigned short *r16 = reinterpret_cast<const unsigned short *>(r);
-                    w[i] = *reinterpret_cast<const uint4 *>(r);
-                    const int cx = cx_of(i);
-                    if (cx > 0) w[i] = shift_from_left(w[i], (unsigned)r16[-1] << 16);
-                    else if (cx < 0) w[i] = shift_from_right(w[i], (unsigned)r16[V]);
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[s]);     // this warp is done with the stage
-                const bool grad = bc_x == BC_GRADIENT;
-                const bool jl = grad && x0 == 0 && t == 0;                  // Eq. 59
-                const bool jr = grad && x0 + W == nx && t == CW * 32 - 1;   // Eq. 60
-                collide_words16<T>(w, k, SeamAdd{jl, jl, jr, jr}, bottom, top);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, w[i]);
-            } else {
+            {     // V nodes per consumer thread
                 C d[8][V];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -258,8 +231,7 @@ constexpr size_t smem_bytes(int stages) {
 }
 
 template <typename T> constexpr int prec_of() {
-    return sizeof(T) == 4 ? PREC_FP32 : sizeof(T) == 8 ? PREC_FP64
-           : (std::is_same<T, __half>::value ? PREC_FP16 : PREC_BF16);
+    return sizeof(T) == 4 ? PREC_FP32 : PREC_FP64;
 }
 
 template <typename T, int CW> constexpr auto kernel_of() { return step_staged<T, CW>; }
@@ -345,6 +317,9 @@ int staged_tile_width(int precision, int consumer_warps) {
 
 bool staged_supported(int precision, int nx, int ny, int consumer_warps) {
     if (consumer_warps != 4 && consumer_warps != 8) return false;
+    // 16-bit storage is kept relative to tile references (refs16.cuh), which
+    // the vector kernels handle; this kernel keeps FP32 and FP64 storage
+    if (precision != PREC_FP32 && precision != PREC_FP64) return false;
     const int w = staged_tile_width(precision, consumer_warps);
     return ny >= 1 && nx >= w && nx % w == 0;
 }
@@ -357,9 +332,7 @@ cudaError_t staged_plan(int precision, int stages, int ctas_per_sm, int consumer
     switch (precision) {
         case PREC_FP32: return plan_t<float>(stages, ctas_per_sm, consumer_warps, l2_hint, out);
         case PREC_FP64: return plan_t<double>(stages, ctas_per_sm, consumer_warps, l2_hint, out);
-        case PREC_FP16: return plan_t<__half>(stages, ctas_per_sm, consumer_warps, l2_hint, out);
-        default:
-            return plan_t<__nv_bfloat16>(stages, ctas_per_sm, consumer_warps, l2_hint, out);
+        default: return cudaErrorNotSupported;     // 16-bit storage: the vector kernels
     }
 }
 
@@ -396,7 +369,5 @@ cudaError_t launch_wait_probe(int *status, cudaStream_t stream) {
                                                const StagedPlan &, int *, cudaStream_t);
 PLBM_STAGED(float)
 PLBM_STAGED(double)
-PLBM_STAGED(__half)
-PLBM_STAGED(__nv_bfloat16)
 
 }  // namespace plbm

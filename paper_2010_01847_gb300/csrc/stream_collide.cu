@@ -42,6 +42,52 @@ step_scalar(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
     }
 }
 
+// The scalar kernel for 16-bit storage (populations stored relative to tile
+// references, refs16.cuh).  Tiles of 8 nodes are 8 aligned lanes, whose sums
+// go through shuffles, so every lane of the warp runs the step: lanes past
+// the lattice's end (whole tiles, as nx is a multiple of 8 then) work on the
+// last node and store nothing.
+template <typename T, bool RES>
+__global__ void __launch_bounds__(256)
+step_scalar16(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long long plane,
+              int bc_x, int bc_y, Coef<float> k, ResidualReq<float> rq) {
+    static_assert(sizeof(T) == 2, "16-bit storage");
+    const long long at = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = at < plane;
+    const long long node = valid ? at : plane - 1;
+    const int y = int(node / nx);
+    const int x = int(node - (long long)y * nx);
+    float loc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float d[8];
+    pull_node<T>(src, plane, nx, ny, x, y, bc_x, bc_y, k, d);
+    if (RES && valid) residual_node(d, k, rq.inv_scale, rq.prev, plane, node, rq.have_prev != 0, loc);
+    float rho, mx, my;
+    moments_f32(d, rho, mx, my);
+    relax_f32(d, rho, mx, my, k);
+    const long long tile = tile_of(k, x, y);
+    const uint4 both = ld_ref_both(src, k, tile);
+    const uint2 enc = make_uint2(both.z, both.w);
+    float Re[8];
+    ref_pops(ref_of<T>(enc), k, Re);
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            dst[(long long)i * plane + node] = Store<T>::put(f_sub(d[i], Re[i]));
+    }
+    if (k.tile_shift == 3) {
+        rho = tile_tree_lanes(rho);
+        mx = tile_tree_lanes(mx);
+        my = tile_tree_lanes(my);
+    }
+    if (valid && (x & ((1 << k.tile_shift) - 1)) == 0)
+        st_ref(dst, k, tile, enc, next_ref<T>(rho, mx, my, k, k.ref_gamma));
+    if (RES) {
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        warp_flush_residual(loc, acc);
+        block_sum5_lane0(acc, rq.partials + (size_t)blockIdx.x * 5);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Vector kernel: each thread owns V consecutive nodes of one row and moves
 // every plane with one aligned 16-byte load and one 16-byte store.  The
@@ -73,7 +119,8 @@ step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
     constexpr int V = Pack<T>::V;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     C d[8][V];
-    const VecPos p = vector_pull<T, SIDES>(src, nx, ny, plane, bc_x, bc_y, k, t, d);
+    uint2 enc = make_uint2(0u, 0u);       // 16-bit storage: the tile's next reference
+    const VecPos p = vector_pull<T, SIDES>(src, nx, ny, plane, bc_x, bc_y, k, t, d, &enc);
     const int y = p.y, x0 = p.x0;
     // the wall rows of Eq. 58 (with SIDES, p.bottom/p.top also flag y sides)
     const bool walls = !SIDES || bc_y == BC_WALLS;
@@ -96,15 +143,19 @@ step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
         }
         if (RES) residual_vec<C, V>(n, k, rq.inv_scale, rq.prev, plane, out, rq.have_prev != 0,
                                     loc);
+        if constexpr (sizeof(T) == 2) {
+            collide_store16<T>(n, k, dst, plane, out, t, enc);     // tile t = vector t
+        } else {
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-            collide(n[j], k);
+            for (int j = 0; j < V; ++j) {
+                collide(n[j], k);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) d[i][j] = n[j][i];
+                for (int i = 0; i < 8; ++i) d[i][j] = n[j][i];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                st_stream(dst + (long long)i * plane + out, Pack<T>::pack(d[i]));
         }
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            st_stream(dst + (long long)i * plane + out, Pack<T>::pack(d[i]));
     }
     if (RES) {
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -132,75 +183,20 @@ __device__ __forceinline__ unsigned ld_u16(const void *p) {
 
 }  // namespace
 
-template <typename T>
-__global__ void __launch_bounds__(256, 4)
-step_vector16(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long long plane,
-              int bc_x, int bc_y, Coef<float> k) {
-    static_assert(sizeof(T) == 2 && Pack<T>::V == 8, "16-bit storage");
-    constexpr int V = 8;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int tpr = nx / V;
-    const long long total = (long long)tpr * ny;
-    const bool active = t < total;
-    const int y = active ? int(t / tpr) : 0;
-    const int xv = active ? int(t - (long long)y * tpr) : 0;
-    const int x0 = xv * V;
-    const int lane = threadIdx.x & 31;
-    const bool walls = bc_y == BC_WALLS;
-    const bool bottom = walls && y == 0;
-    const bool top = walls && y == ny - 1;
-    const bool need_left = (lane == 0 || xv == 0) && active;
-    const bool need_right = (lane == 31 || xv + 1 == tpr) && active;
-    const int sx_left = x0 == 0 ? nx - 1 : x0 - 1;
-    const int sx_right = x0 + V >= nx ? x0 + V - nx : x0 + V;
+// Resident 256-thread blocks per SM the node-pair residual step is compiled
+// for (registers per thread = 65536 / (256 x blocks)); the plain 16-bit
+// steps run the pipelined kernel of pipe16.cu.
+#ifndef PLBM_V16_RES_BLOCKS
+#define PLBM_V16_RES_BLOCKS 2
+#endif
 
-    // every load first (the vectors and the edge elements), as in vector_pull
-    uint4 w[8];
-    unsigned edge[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i);
-        int sy = y - cy;
-        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-        const long long row = (long long)i * plane + (long long)sy * nx;
-        const bool unknown = (cy > 0 && bottom) || (cy < 0 && top);
-        w[i] = (active && !unknown) ? ld_stream(src + row + x0) : make_uint4(0u, 0u, 0u, 0u);
-        edge[i] = 0u;
-        if (cx > 0 && need_left && !unknown) edge[i] = ld_u16(src + row + sx_left);
-        if (cx < 0 && need_right && !unknown) edge[i] = ld_u16(src + row + sx_right);
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int cx = cx_of(i);
-        if (cx > 0) {
-            unsigned nb = __shfl_up_sync(0xffffffffu, w[i].w, 1);
-            if (need_left) nb = edge[i] << 16;
-            w[i] = shift_from_left(w[i], nb);
-        } else if (cx < 0) {
-            unsigned nb = __shfl_down_sync(0xffffffffu, w[i].x, 1);
-            if (need_right) nb = edge[i];
-            w[i] = shift_from_right(w[i], nb);
-        }
-    }
-    if (!active) return;
-    // at a warp edge or a row end the neighbour was loaded: the seam jump
-    // (zero away from the seam) is added there, as vector_pull does
-    const bool grad = bc_x == BC_GRADIENT;
-    const SeamAdd seam{need_left, x0 == 0 && grad, need_right, x0 + V == nx && grad};
-    collide_words16<T>(w, k, seam, bottom, top);
-    const long long out = (long long)y * nx + x0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, w[i]);
-}
-
-// The same step that also reduces the residual of the pulled state
-// (residual_terms on each node in node order, the history planes read and
-// written as node pairs): the sums the node-by-node kernel forms.  A kernel
-// of its own rather than a template flag on step_vector16: the plain step's
-// register allocation, and with it its speed, moved when the two shared one
-// body (358 against 331 us per step at 8192^2).
+// The 16-bit step that also reduces the residual of the pulled state (one
+// step in many): one thread per 16-byte vector, the node pairs of
+// pairs16.cuh with the tile references, residual_terms on each node in node
+// order (the history planes read and written as node pairs): the sums the
+// node-by-node kernel forms.
 template <typename T>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, PLBM_V16_RES_BLOCKS)
 step_vector16_res(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
                   long long plane, int bc_x, int bc_y, Coef<float> k, ResidualReq<float> rq) {
     static_assert(sizeof(T) == 2 && Pack<T>::V == 8, "16-bit storage");
@@ -221,6 +217,7 @@ step_vector16_res(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny
     const int sx_left = x0 == 0 ? nx - 1 : x0 - 1;
     const int sx_right = x0 + V >= nx ? x0 + V - nx : x0 + V;
 
+    const VecRefWords rw = vector_ref_loads<T>(src, k, ny, y, xv, need_left, need_right);
     uint4 w[8];
     unsigned edge[8];
 #pragma unroll
@@ -248,6 +245,10 @@ step_vector16_res(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny
             w[i] = shift_from_right(w[i], nb);
         }
     }
+    float Rd[8], Rx[8];
+    uint2 enc;
+    vector_ref_pops<T>(rw, k, need_left, need_right, Rd, Rx, enc);
+    pull_edge_refs(Rd, Rx, need_left, need_right);
     float loc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (active) {
         const bool grad = bc_x == BC_GRADIENT;
@@ -273,9 +274,13 @@ step_vector16_res(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny
             for (int q = 0; q < 3; ++q)
                 *reinterpret_cast<float2 *>(rq.prev + q * plane + out + 2 * m) = h[q];
         };
-        collide_words16<T>(w, k, seam, bottom, top, residual);
+        float sums[3];
+        float Re[8];
+        ref_pops(ref_of<T>(enc), k, Re);
+        collide_words16<T>(w, k, seam, bottom, top, Rd, Rx, Re, sums, residual);
 #pragma unroll
         for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, w[i]);
+        st_ref(dst, k, t, enc, next_ref<T>(sums[0], sums[1], sums[2], k, k.ref_gamma));
     }
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     warp_flush_residual(loc, acc);
@@ -321,9 +326,15 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
     // single steps of a cluster-resident lattice (the residual step) run on
     // the vector kernel when nx allows, else the scalar one
     if (kernel == KERNEL_RESIDENT) kernel = nx % Pack<T>::V == 0 ? KERNEL_VECTOR : KERNEL_SCALAR;
-    if (kernel == KERNEL_STAGED)
-        return launch_step_staged<T>(src, dst, nx, ny, bc_x, bc_y, k, status, plan, blocks_out,
-                                     stream);
+    if constexpr (sizeof(T) == 2) {
+        // the staged kernel keeps FP32 / FP64 storage only (16-bit storage
+        // with tile references runs on the vector kernels)
+        if (kernel == KERNEL_STAGED) return cudaErrorNotSupported;
+    } else {
+        if (kernel == KERNEL_STAGED)
+            return launch_step_staged<T>(src, dst, nx, ny, bc_x, bc_y, k, status, plan,
+                                         blocks_out, stream);
+    }
     const ResidualReq<typename Store<T>::C> none{};
     const long long threads = kernel == KERNEL_VECTOR ? plane / Pack<T>::V : plane;
     const int bs = step_block_size(threads);
@@ -347,12 +358,18 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
                                                                 bc_y, k, *rq);
         } else {
             if constexpr (sizeof(T) == 2)
-                step_vector16<T><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
-                                                            k);
+                return launch_step_pipe16<T>(src, dst, nx, ny, bc_x, bc_y, k, stream);
             else
                 step_vector<T, false><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
                                                                  bc_y, k, none);
         }
+    } else if constexpr (sizeof(T) == 2) {
+        if (rq)
+            step_scalar16<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                              bc_y, k, *rq);
+        else
+            step_scalar16<T, false><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                               bc_y, k, none);
     } else {
         if (rq)
             step_scalar<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,

@@ -9,7 +9,7 @@
 // handles that.  Every lane of a warp must call it (shuffles).
 #pragma once
 
-#include "lbm_device.cuh"
+#include "refs16.cuh"
 
 namespace plbm {
 
@@ -141,11 +141,17 @@ struct VecPos {
 // With SIDES, directions created with BC_SIDES are not periodic either:
 // populations that would come from beyond a side are left at 0 for the
 // caller's apply_sides (bottom/top then also flag the rows of y sides).
+// 16-bit storage: the values are stored relative to tile references
+// (refs16.cuh); each is pulled with its tile's reference population added
+// (before the shift, so the neighbour's value arrives complete), and *enc
+// (if given) receives the reference this thread's tile is stored against
+// next.
 template <typename T, bool SIDES = false>
 __device__ __forceinline__ VecPos vector_pull(const T *__restrict__ src, int nx, int ny,
                                               long long plane, int bc_x, int bc_y,
                                               const Coef<typename Store<T>::C> &k, long long t,
-                                              typename Store<T>::C (&d)[8][Pack<T>::V]) {
+                                              typename Store<T>::C (&d)[8][Pack<T>::V],
+                                              uint2 *enc = nullptr) {
     using C = typename Store<T>::C;
     constexpr int V = Pack<T>::V;
     const int tpr = nx / V;
@@ -169,6 +175,8 @@ __device__ __forceinline__ VecPos vector_pull(const T *__restrict__ src, int nx,
     const bool need_right = (lane == 31 || xv + 1 == tpr) && active;
     const int sx_left = x0 == 0 ? nx - 1 : x0 - 1;
     const int sx_right = x0 + V >= nx ? x0 + V - nx : x0 + V;
+    VecRefWords rw{};
+    if constexpr (sizeof(T) == 2) rw = vector_ref_loads<T>(src, k, ny, y, xv, need_left, need_right);
     C edge[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -190,6 +198,18 @@ __device__ __forceinline__ VecPos vector_pull(const T *__restrict__ src, int nx,
             edge[i] = Store<T>::load(src[row + sx_right]);
     }
 
+    if constexpr (sizeof(T) == 2) {
+        float Rd[8], Rx[8];
+        uint2 e2;
+        vector_ref_pops<T>(rw, k, need_left, need_right, Rd, Rx, e2);
+        if (enc) *enc = e2;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) d[i][j] = f_add(d[i][j], Rd[i]);
+            if (cx_of(i) != 0) edge[i] = f_add(edge[i], Rx[i]);
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int cx = cx_of(i);
@@ -219,9 +239,11 @@ __device__ __forceinline__ VecPos vector_pull(const T *__restrict__ src, int nx,
 }
 
 // Loads the thread's V nodes of a stored state (no streaming): step 0.
+// 16-bit storage: each value with its own tile's reference population.
 template <typename T>
 __device__ __forceinline__ VecPos vector_local(const T *__restrict__ src, int nx, int ny,
                                                long long plane, long long t,
+                                               const Coef<typename Store<T>::C> &k,
                                                typename Store<T>::C (&d)[8][Pack<T>::V]) {
     using C = typename Store<T>::C;
     constexpr int V = Pack<T>::V;
@@ -240,7 +262,44 @@ __device__ __forceinline__ VecPos vector_local(const T *__restrict__ src, int nx
             for (int j = 0; j < V; ++j) d[i][j] = C(0);
         }
     }
+    if constexpr (sizeof(T) == 2) {
+        if (active) {
+            const Ref3 a = ref_of<T>(ld_ref_stored(src, k, t));     // tile t = vector t
+            float R[8];
+            ref_pops(a, k, R);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < V; ++j) d[i][j] = f_add(d[i][j], R[i]);
+        }
+    }
     return VecPos{y, xv, x0, active, false, false};
+}
+
+// 16-bit storage, node by node: collides the thread's 8 pulled nodes n[j]
+// (boundaries applied), stores them (tile `tile` of dst, row offset `out`)
+// less the reference populations of `enc` and writes the tile's references
+// {enc, the next one from the nodes' moments} (refs16.cuh).
+template <typename T>
+__device__ __forceinline__ void collide_store16(float (&n)[8][8], const Coef<float> &k,
+                                                T *__restrict__ dst, long long plane,
+                                                long long out, long long tile, uint2 enc) {
+    float rho[8], mx[8], my[8], Re[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        moments_f32(n[j], rho[j], mx[j], my[j]);
+        relax_f32(n[j], rho[j], mx[j], my[j], k);
+    }
+    ref_pops(ref_of<T>(enc), k, Re);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = f_sub(n[j][i], Re[i]);
+        st_stream(dst + (long long)i * plane + out, Pack<T>::pack(v));
+    }
+    st_ref(dst, k, tile, enc,
+           next_ref<T>(tile_tree8(rho), tile_tree8(mx), tile_tree8(my), k, k.ref_gamma));
 }
 
 }  // namespace plbm

@@ -1,5 +1,7 @@
 """Shared test helpers: error metrics and paired GPU/oracle runs."""
+import json
 import math
+import os
 
 import numpy as np
 
@@ -49,10 +51,23 @@ def oracle_run(nx, ny, tau_N, tau_R, fields, steps, bc_x=0, bc_y=0, delta_e=0.0)
     return lat
 
 
+def record_errors(precision, err_e, err_q):
+    """Append the measured errors of the running test to the JSON-lines file
+    named by PLBM_ERROR_LOG, when that variable is set (error tables)."""
+    path = os.environ.get("PLBM_ERROR_LOG")
+    if not path:
+        return
+    with open(path, "a") as fh:
+        fh.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", ""),
+                             "precision": precision, "err_e": float(err_e),
+                             "err_q": float(err_q)}) + "\n")
+
+
 def check_gate(precision, err_e, err_q, sanity=None):
     """Pass within the gate; for 16-bit storage record a miss within the
     sanity bound as xfail (with the measured errors); otherwise fail."""
     import pytest
+    record_errors(precision, err_e, err_q)
     tol = TOL[precision]
     if err_e <= tol and err_q <= tol:
         return

@@ -37,7 +37,11 @@ def test_tau_from_kn_and_sizes(lib):
     assert plbm.tau_from_kn(0.01, 31.0) == pytest.approx(0.01 * 31 * math.sqrt(0.6), rel=1e-15)
     g = plbm.Grid(128, 32)
     assert lib.lbm_population_bytes(g, plbm.FP32) == 8 * 128 * 32 * 4
-    assert lib.lbm_population_bytes(g, plbm.FP16_DEV) == 8 * 128 * 32 * 2
+    # 16-bit storage: 8 planes, then 8 reference values per tile of 8 nodes
+    # (nx a multiple of 8) or of one node
+    assert lib.lbm_population_bytes(g, plbm.FP16_DEV) == (8 * 128 * 32 + 8 * 16 * 32) * 2
+    assert lib.lbm_population_bytes(g, plbm.BF16_DEV) == (8 * 128 * 32 + 8 * 16 * 32) * 2
+    assert lib.lbm_population_bytes(plbm.Grid(37, 29), plbm.FP16_DEV) == 16 * 37 * 29 * 2
     assert lib.lbm_population_bytes(g, plbm.FP64) == 8 * 128 * 32 * 8
     assert lib.lbm_population_bytes(plbm.Grid(0, 3), plbm.FP32) == 0
     assert lib.lbm_population_bytes(g, 9) == 0

@@ -26,7 +26,13 @@ CASES = [
     (200, 72, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 2e-3, "vector", "fp32", None),
     (96, 33, plbm.PERIODIC, plbm.PERIODIC, 0.0, "vector", "fp16", None),
     (2048, 24, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3, "staged", "fp32", None),
-    (4096, 9, plbm.PERIODIC_GRADIENT, plbm.PERIODIC, -1e-3, "staged", "bf16", None),
+    (4096, 9, plbm.PERIODIC_GRADIENT, plbm.PERIODIC, -1e-3, "vector", "bf16", None),
+    # 16-bit storage on the scalar kernel: tiles of 8 nodes (nx % 8 == 0) and of one node
+    (96, 33, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3, "scalar", "bf16", None),
+    (37, 29, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3, "scalar", "fp16", None),
+    (200, 40, S, S, 0.0, "vector", "fp16",
+     [(plbm.ISOTHERMAL, 1.0), (plbm.ISOTHERMAL, 1.0), (plbm.ISOTHERMAL, 1.0),
+      (plbm.HEAT_FLUX, 1e-4)]),
     (1024, 2, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3, "staged", "fp64", None),
     (1, 1, plbm.PERIODIC, plbm.PERIODIC, 0.0, "scalar", "fp32", None),
     (41, 41, S, S, 0.0, "scalar", "fp32",

@@ -53,8 +53,8 @@ def _kernel_ok(kernel, nx, precision):
     v = VEC[precision]
     if kernel == "vector":
         return nx % v == 0
-    if kernel == "staged":
-        return nx % (256 * v) == 0
+    if kernel == "staged":               # FP32 / FP64 storage only
+        return precision in ("fp32", "fp64") and nx % (256 * v) == 0
     if kernel == "resident":
         return precision == "fp32"          # every lattice here fits one cluster
     return True
@@ -108,7 +108,7 @@ def test_parity_degenerate_relaxation(tau_N, tau_R):
     assert err_e <= TOL["fp32"] and err_q <= TOL["fp32"], (err_e, err_q)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("shape", [(2, 0, 4, 0), (3, 1, 8, 1), (6, 0, 4, 1), (2, 2, 8, 0)])
 def test_staged_shapes_agree_bitwise(precision, shape):
     """Every staged launch shape (ring depth, CTAs/SM, consumer warps, L2
@@ -152,8 +152,11 @@ def test_kernels_and_graph_chunks_agree_bitwise(precision):
     nx, ny = 2048, 40
     fields = inputs.random_state_fields(nx, ny, seed=5)
     outs = []
-    for kernel, chunk in [("scalar", 0), ("vector", 0), ("vector", 64), ("staged", 0),
-                          ("staged", 64), ("auto", 16)]:
+    runs = [("scalar", 0), ("vector", 0), ("vector", 64), ("staged", 0), ("staged", 64),
+            ("auto", 16)]
+    for kernel, chunk in runs:
+        if kernel == "staged" and precision != "fp32":
+            continue                      # the staged kernel keeps FP32 / FP64 storage
         g = gpu_run(nx, ny, 0.8, 9.0, fields, 150, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS,
                     1e-3, precision, kernel, graph_chunk=chunk)
         outs.append(g.populations())
@@ -286,6 +289,8 @@ def test_residual_matches_oracle_definition():
 @pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16"])
 def test_fused_step_residual_matches_separate_pass(kernel, precision):
     """lbm_step_residual == lbm_step + lbm_residual: same r, energy and state."""
+    if kernel == "staged" and precision == "fp16":
+        pytest.skip("the staged kernel keeps FP32 / FP64 storage")
     nx, ny = 2048, 20
     fields = inputs.random_state_fields(nx, ny, seed=31)
     bc = (plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3)
