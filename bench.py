@@ -11,10 +11,14 @@ into that step's launch.  The population buffers (2 x 2.1 GB) exceed
 the 129 MB L2, so no flush is needed between steps.
 
 Metric: GLUPS (10^9 lattice-site updates per second, whole job).  Also
-reported: the roofline of the stream-collide kernel (algorithmic bytes
-16 x sizeof(storage) per site update over its CUDA-event time), an
-end-to-end figure through the public API with host buffers, and the FP64
-oracle on the host cores as a CPU baseline.
+reported: the roofline of the stream-collide kernel (algorithmic bytes: one
+state buffer read and one written per site update, over its CUDA-event
+time), an end-to-end figure through the public API with host buffers, the
+FP64 oracle on the host cores as a CPU baseline, and (``steady_state``) the
+metric's second half: time to steady state (r < 1e-8) of 64 held-out
+channels from the cold, the analytic (Eq. 68) and the learned start, with
+each end state's error against an FP64 reference (``--no-steady`` skips it;
+``--workload warmstart`` runs the full 512-channel study).
 
 Multi-GPU: ``--gpus N`` (under torchrun) runs N independent replicas, one
 lattice per rank, with no data-path collective (weak scaling); the job time
@@ -59,6 +63,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32", choices=list(STORAGE_BYTES))
     ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
+                    help="rounding of 16-bit storage")
     ap.add_argument("--nx", type=int, default=inputs.THROUGHPUT_8192.nx)
     ap.add_argument("--ny", type=int, default=inputs.THROUGHPUT_8192.ny)
     ap.add_argument("--no-e2e", action="store_true")
@@ -81,6 +87,11 @@ def parse():
                     help="steps per residual window (FP32 rounding puts a floor of about "
                          "1e-6/K under the residual of high-tau channels)")
     ap.add_argument("--max-steps", type=int, default=400000)
+    ap.add_argument("--reference-instances", type=int, default=64,
+                    help="held-out channels whose end states are compared with an FP64 "
+                         "reference (warmstart workload)")
+    ap.add_argument("--no-steady", action="store_true",
+                    help="default workload: skip the time-to-steady-state leg")
     ap.add_argument("--sequential-sample", type=int, default=16)
     return ap.parse_args()
 
@@ -349,7 +360,8 @@ def run_native(args):
     e_dev = torch.from_numpy(e).to(dev)
     z_dev = torch.zeros_like(e_dev)
 
-    lat = plbm.Lattice(nx, ny, tau_N, tau_R, precision=args.precision, kernel=args.kernel)
+    lat = plbm.Lattice(nx, ny, tau_N, tau_R, precision=args.precision, kernel=args.kernel,
+                       rounding=args.rounding if STORAGE_BYTES[args.precision] == 2 else "nearest")
     lat.init(e_dev, z_dev, z_dev)
     tuned = None
     if args.kernel == "auto":
@@ -457,6 +469,17 @@ def run_native(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(w, args.cpu_seconds)
 
+    # time to steady state, learned vs analytic vs cold start (the metric's
+    # second half), on a bounded held-out set: one GPU, rank 0 alone
+    kernel_name = lat.kernel
+    staged_shape = lat.staged_config if kernel_name == "staged" else None
+    steady = None
+    if rank == 0 and world == 1 and not args.no_steady:
+        lat.close()
+        torch.cuda.synchronize()
+        steady = steady_state_study(n_train=1024, train_steps=2000, n_test=64, n_ref=64,
+                                    tol=1e-8, check_every=500, max_steps=400000)
+
     if rank == 0:
         clocks = sampler.summary()
         line = {
@@ -468,15 +491,17 @@ def run_native(args):
             "config": {"workload": f"heat_mode_{nx}x{ny}", "lattice": "D2Q8 (paper's D2Q9 "
                        "label: rest population identically zero, not stored)",
                        "kn_N": w["kn_N"], "kn_R": w["kn_R"], "length_cells": w["length"],
-                       "storage": f"{args.precision} deviation" if args.precision != "fp64"
-                       else "fp64 deviation", "kernel": lat.kernel,
-                       "staged_shape": lat.staged_config if lat.kernel == "staged" else None,
+                       "storage": (f"{args.precision} deviation" +
+                                   (f", tile references, {args.rounding} rounding"
+                                    if STORAGE_BYTES[args.precision] == 2 else "")),
+                       "kernel": kernel_name,
+                       "staged_shape": staged_shape,
                        "autotuned": tuned is not None,
                        "residual_every": window,
                        "l2": "inputs larger than L2 (2 x population buffers >> 129 MB); "
                              "no flush", "parallelism": f"replicas x{world}"},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches,
-            "e2e": e2e, "cpu_baseline": cpu,
+            "e2e": e2e, "cpu_baseline": cpu, "steady_state": steady,
         }
         print(json.dumps(line), flush=True)
     lat.close()
@@ -704,60 +729,106 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def run_warmstart(args):
-    """Learned warm start: steady states of seeded training channels from the
-    batched solver, the network trained on the GPU, then held-out channels
-    (length 4W, a seed the training never saw) solved to r < tol from the
-    cold start and from the predicted profiles."""
+def steady_state_study(n_train, train_steps, n_test, n_ref, tol, check_every, max_steps,
+                       w_range=(16, 512)):
+    """Time to steady state (r < tol) of held-out walled channels with the
+    periodic gradient from three starts, and their accuracy.
+
+    Training: n_train channels' steady states from the batched solver (on
+    channels shortened to 8 columns, whose steady rows are the full ones'),
+    the network trained on the GPU (train_steps Adam steps, minibatches of
+    512).  Held-out: n_test channels of length 4W from a seed training never
+    saw, solved from the cold start (e = e_ref, q = 0), the analytic start
+    (Eq. 68 flux, affine e) and the learned start.  Reference: the first
+    n_ref held-out channels solved with FP64 storage to r < 1e-12 (shortened
+    copies); each start's end state is compared with it row by row."""
     import torch
-    torch.cuda.set_device(0)
     from paper_2010_01847_gb300 import warmstart
     t0 = time.perf_counter()
-    train = warmstart.channels(args.train_instances, seed=inputs.SEED + 1,
-                               nx=warmstart.TRAIN_NX)
-    prof, tsteps, tr, t_gen = warmstart.steady_profiles(train, args.tol, args.check_every)
-    ws = warmstart.WarmStart(seed=0, max_batch=max(512, args.train_instances))
+    train = warmstart.channels(n_train, seed=inputs.SEED + 1, nx=warmstart.TRAIN_NX,
+                               w_range=w_range)
+    prof, tsteps, tr, t_gen = warmstart.steady_profiles(train, tol, check_every, max_steps)
+    ws = warmstart.WarmStart(seed=0, max_batch=max(512, n_train))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    hist = ws.train(warmstart.features(train), prof, steps=args.train_steps, batch=512, lr=1e-3)
+    hist = ws.train(train, prof, steps=train_steps, batch=512, lr=1e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
-    test = warmstart.channels(args.instances, seed=inputs.SEED + 2)
+    test = warmstart.channels(n_test, seed=inputs.SEED + 2, w_range=w_range)
     t2 = time.perf_counter()
     pred = ws.predict(test)
     torch.cuda.synchronize()
     t_pred = time.perf_counter() - t2
-    cold_steps, cold_r, t_cold, cold = warmstart.solve(test, None, args.tol, args.check_every,
-                                                       args.max_steps)
-    warm_steps, warm_r, t_warm, warm = warmstart.solve(test, pred, args.tol, args.check_every,
-                                                       args.max_steps)
+    t3 = time.perf_counter()
+    ana = warmstart.analytic_profiles(test)
+    torch.cuda.synchronize()
+    t_ana = time.perf_counter() - t3
+    runs = {}
+    for name, start in (("cold", None), ("analytic", ana), ("learned", pred)):
+        steps, r, secs, b = warmstart.solve(test, start, tol, check_every, max_steps)
+        runs[name] = {"seconds": secs, "steps": steps, "r": r, "batch": b}
+    ref_set = test[:n_ref]
+    t4 = time.perf_counter()
+    ref, rsteps, rr = warmstart.reference_profiles(ref_set)
+    t_ref = time.perf_counter() - t4
     sites = np.array([i["nx"] * i["ny"] for i in test], dtype=np.float64)
-    # agreement of the two steady states (relative to each field's range)
-    de, dq = 0.0, 0.0
-    for k in range(len(test)):
-        ce, cq, _ = cold.moments(k)
-        we, wq, _ = warm.moments(k)
-        de = max(de, float(np.abs(we - ce).max() / max(np.abs(ce - ce.mean()).max(), 1e-300)))
-        dq = max(dq, float(np.abs(wq - cq).max() / max(np.abs(cq).max(), 1e-300)))
+    out = {"tol": tol, "check_every": check_every,
+           "train_instances": len(train), "train_steps": train_steps,
+           "held_out": len(test), "widths": list(w_range)}
+    for name, run in runs.items():
+        b = run["batch"]
+        ee, eq = warmstart.profile_errors(b.profiles()[:n_ref], ref, ref_set)
+        out[name] = {"seconds": run["seconds"],
+                     "steps_median": float(np.median(run["steps"])),
+                     "steps_max": int(run["steps"].max()),
+                     "site_updates": float((run["steps"] * sites).sum()),
+                     "converged": bool(np.all(run["r"] < tol)),
+                     "err_vs_reference": {"e_max": float(ee.max()), "q_max": float(eq.max()),
+                                          "e_median": float(np.median(ee)),
+                                          "q_median": float(np.median(eq))}}
+        b.close()
+    out["speedup_learned_vs_cold"] = out["cold"]["seconds"] / out["learned"]["seconds"]
+    out["speedup_learned_vs_analytic"] = out["analytic"]["seconds"] / out["learned"]["seconds"]
+    out["speedup_analytic_vs_cold"] = out["cold"]["seconds"] / out["analytic"]["seconds"]
+    out["training"] = {"data_generation_seconds": t_gen,
+                       "data_steps_median": float(np.median(tsteps)),
+                       "train_seconds": t_train, "loss_first": float(hist[0]),
+                       "loss_last": float(hist[-1]), "predict_seconds": t_pred}
+    out["analytic_profile_seconds"] = t_ana
+    # the whole learned pipeline (generate data, train, predict, solve)
+    out["learned_pipeline_seconds"] = t_gen + t_train + t_pred + out["learned"]["seconds"]
+    out["speedup_learned_pipeline_vs_cold"] = out["cold"]["seconds"] / \
+        out["learned_pipeline_seconds"]
+    out["reference"] = {"channels": len(ref_set), "storage": "fp64", "tol": 1e-12,
+                        "seconds": t_ref, "converged": bool(np.all(rr < 1e-12)),
+                        "how": "held-out channels shortened to 8 columns with the same "
+                               "gradient (their steady rows are the full channels'), "
+                               "solved to r < 1e-12"}
+    out["study_seconds"] = time.perf_counter() - t0
+    return out
+
+
+def run_warmstart(args):
+    """Learned warm start on the full held-out set: steady states of seeded
+    training channels from the batched solver, the network trained on the
+    GPU, then held-out channels (length 4W, a seed the training never saw)
+    solved to r < tol from the cold, analytic and learned starts, each end
+    state against an FP64 reference."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2010_01847_gb300 import warmstart
+    st = steady_state_study(args.train_instances, args.train_steps, args.instances,
+                            min(args.instances, args.reference_instances), args.tol,
+                            args.check_every, args.max_steps)
     line = {
-        "metric": "time to steady state (r < 1e-8), held-out channels, warm vs cold start",
-        "value": t_warm, "unit": "s", "n_gpus": 1, "higher_is_better": False,
+        "metric": "time to steady state (r < 1e-8), held-out channels, learned vs cold start",
+        "value": st["learned"]["seconds"], "unit": "s", "n_gpus": 1, "higher_is_better": False,
         "dtype": "f32 solve / bf16 network", "data": "synthetic",
-        "config": {"workload": f"warm_start_{len(test)}_held_out", "tol": args.tol,
+        "config": {"workload": f"warm_start_{st['held_out']}_held_out", "tol": args.tol,
                    "check_every": args.check_every,
-                   "train_instances": len(train), "train_steps": args.train_steps,
+                   "train_instances": st["train_instances"], "train_steps": args.train_steps,
                    "network": list(warmstart.WIDTHS)},
-        "cold_seconds": t_cold, "warm_seconds": t_warm, "speedup": t_cold / t_warm,
-        "cold_steps": {"median": float(np.median(cold_steps)), "max": int(cold_steps.max()),
-                       "site_updates": float((cold_steps * sites).sum())},
-        "warm_steps": {"median": float(np.median(warm_steps)), "max": int(warm_steps.max()),
-                       "site_updates": float((warm_steps * sites).sum())},
-        "all_converged": bool(np.all(cold_r < args.tol) and np.all(warm_r < args.tol)),
-        "steady_state_agreement": {"max_rel_e": de, "max_rel_q": dq},
-        "training": {"data_generation_seconds": t_gen, "data_steps_median": float(np.median(tsteps)),
-                     "train_seconds": t_train, "loss_first": hist[0], "loss_last": hist[-1],
-                     "predict_seconds": t_pred},
-        "total_seconds": time.perf_counter() - t0,
+        "steady_state": st,
     }
     print(json.dumps(line), flush=True)
 

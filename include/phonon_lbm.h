@@ -261,6 +261,22 @@ lbm_status lbm_set_kernel(lbm_ctx *ctx, int kernel);
 /* The kernel lbm_step will launch (never LBM_KERNEL_AUTO). */
 int lbm_get_kernel(const lbm_ctx *ctx);
 
+/* Rounding of 16-bit storage (FP16 / BF16 deviations; no counterpart in the
+ * paper, which states no precision).  LBM_ROUND_NEAREST (the default) rounds
+ * every stored population to nearest even.  LBM_ROUND_STOCHASTIC rounds up
+ * with probability equal to the dropped fraction of the value, so the
+ * rounding error is zero on average and the errors of a slowly varying
+ * field add like a random walk over many steps instead of building up; the
+ * random bits are a hash of the node pair, the plane and the two values, so
+ * a run is deterministic and every kernel stores the same bits.  It costs
+ * instructions (about a third more in the node-pair kernel); round to
+ * nearest converges to an exact fixed point at steady state, stochastic
+ * rounding to within its noise.  Drops the context's captured graphs.
+ * Errors: EINVAL (NULL, unknown mode), EUNSUPPORTED (stochastic with FP32 or
+ * FP64 storage). */
+typedef enum { LBM_ROUND_NEAREST = 0, LBM_ROUND_STOCHASTIC = 1 } lbm_rounding;
+lbm_status lbm_set_rounding(lbm_ctx *ctx, int rounding);
+
 /* Set the treatment of one side of an LBM_BC_SIDES direction (Section 2.5;
  * see lbm_side_kind).  side: LBM_SIDE_*; kind: LBM_SIDE_*; value: e_s (the
  * side's energy density, same units as e) for ISOTHERMAL, q_0 (the heat
@@ -396,17 +412,34 @@ lbm_status lbm_batch_autotune(lbm_batch *batch, int trial_steps, double *us_per_
  * Y = j/255 across the channel (row means, linear interpolation), with the
  * Fourier flux q_F = (5/9) tau_R delta_e / nx (Eqs. 59-60 fix the slope
  * |de/dx| = delta_e / nx); entries 256..511 are E(Y) = (row mean of
- * e + delta_e (x - (nx-1)/2) / nx - e_ref) / delta_e.  Synchronous. */
+ * e + delta_e (x - (nx-1)/2) / nx - e_ref) nx / delta_e, in units of the
+ * drop per cell.  Both are set by the gradient alone, so they do not depend
+ * on the channel's length.  Synchronous. */
 lbm_status lbm_batch_profiles(lbm_batch *batch, float *out);
 
 /* Step 0 of every instance from DEVICE profiles in the layout of
  * lbm_batch_profiles (the learned warm start): q_x = Q(Y) q_F, q_y = 0,
- * e = e_ref + delta_e (E(Y) - <E> - (x - (nx-1)/2) / nx), then Eq. 15, where
+ * e = e_ref + (delta_e / nx) (E(Y) - <E> - (x - (nx-1)/2)), then Eq. 15, where
  * <E> is the row mean of E: a channel conserves its total energy, so the
  * start keeps the cold start's mean energy and reaches the same steady
  * state.  FP32 or FP64 storage.  Resets steps, history and retirement.
  * Synchronous. */
 lbm_status lbm_batch_init_profiles(lbm_batch *batch, const float *profiles);
+
+/* The analytic start, as profiles in the layout of lbm_batch_profiles: Q(Y)
+ * from Eq. 68 (the heat flux of the phonon hydrodynamic model across a
+ * channel between diffuse walls, over the Fourier flux) with
+ * Kn_eff = sqrt(tau_C tau_R v_g^2 / 5) / d and Kn_C = v_g tau_C / d in
+ * lattice units (v_g = sqrt(5/3), d = ny - 1), and E(Y) = 0 (e affine in x
+ * with the steady slope).  For count instances (walls on y, ny >= 2, finite
+ * tau_R; nx and delta_e do not enter) into the DEVICE float array out
+ * [count][512]: op 0 writes them, op 1 adds them to out, op -1 subtracts
+ * them (a learned correction to the analytic profile is trained on the
+ * difference and added back).  stream: cudaStream_t (NULL = legacy
+ * default).  Allocates a temporary device copy for op != 0.  Synchronous.
+ * Errors (text from lbm_last_error(NULL)): EINVAL, EUNSUPPORTED, ECUDA. */
+lbm_status lbm_analytic_profiles(const lbm_instance *inst, int count, float *out, int op,
+                                 void *stream);
 
 /* Running (not retired) instances, and the steps instance i has run. */
 long lbm_batch_active(const lbm_batch *batch);
@@ -448,6 +481,22 @@ lbm_status lbm_mlp_loss_grad(lbm_mlp *mlp, const float *x, const float *t, int b
  * *loss is the loss before the update.  Synchronous. */
 lbm_status lbm_mlp_train_step(lbm_mlp *mlp, const float *x, const float *t, int batch,
                               float lr, double *loss);
+/* `steps` Adam steps (as lbm_mlp_train_step) on minibatches of `batch` rows
+ * drawn from n training pairs, DEVICE float x [n][in] and t [n][out], run
+ * entirely on the device: one step (minibatch gather, forward, backward,
+ * Adam) is captured once as a CUDA graph and replayed, with no host
+ * round trip between steps.  Step s (0-based) draws row j of its minibatch
+ * as sample SplitMix64(seed ^ (s batch + j)) mod n (with replacement; all n
+ * rows in order when batch >= n) and uses the learning rate
+ * lr_final + (lr - lr_final)(1 + cos(pi s / steps)) / 2.  The Adam step
+ * count carries over between calls.  loss (HOST, `steps` floats, may be
+ * NULL) receives each step's loss before its update.  Allocates the
+ * minibatch buffers on the first call and the loss history for the call.
+ * Synchronous.  Errors: EINVAL (NULL inputs, n < 1, batch out of range,
+ * steps < 0, learning rates <= 0), ENOMEM, ECUDA. */
+lbm_status lbm_mlp_train(lbm_mlp *mlp, const float *x, const float *t, int n, int batch,
+                         long steps, float lr, float lr_final, unsigned long long seed,
+                         float *loss);
 const char *lbm_mlp_last_error(const lbm_mlp *mlp);
 
 /* ---- Residual without device allocation ---------------------------------

@@ -29,6 +29,8 @@ KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_STAGED, KERNEL_RESIDENT = 0, 1
 
 D1Q2, D3Q14 = 1, 3                                     # lbm_lattice
 PRECISIONS = {"fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV, "fp64": FP64}
+ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1
+ROUNDINGS = {"nearest": ROUND_NEAREST, "stochastic": ROUND_STOCHASTIC}
 KERNELS = {"auto": KERNEL_AUTO, "scalar": KERNEL_SCALAR, "vector": KERNEL_VECTOR,
            "staged": KERNEL_STAGED, "resident": KERNEL_RESIDENT}
 _ELEM = {FP32: 4, FP16_DEV: 2, BF16_DEV: 2, FP64: 8}
@@ -41,16 +43,17 @@ EXPORTS = [
     "lbm_step_residual",
     "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_step_count",
     "lbm_set_kernel", "lbm_get_kernel", "lbm_set_side", "lbm_get_side",
-    "lbm_set_staged_config", "lbm_get_staged_config",
+    "lbm_set_staged_config", "lbm_get_staged_config", "lbm_set_rounding",
     "lbm_set_graph_chunk", "lbm_autotune",
     "lbm_kernel_launches", "lbm_storage_scale", "lbm_last_error",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_init", "lbm_batch_step",
     "lbm_batch_residuals", "lbm_batch_solve", "lbm_batch_moments", "lbm_batch_set_schedule",
     "lbm_batch_get_schedule", "lbm_batch_autotune", "lbm_batch_active", "lbm_batch_steps",
     "lbm_batch_last_error", "lbm_batch_profiles", "lbm_batch_init_profiles",
+    "lbm_analytic_profiles",
     "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_param_count", "lbm_mlp_set_params",
     "lbm_mlp_get_params", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train_step",
-    "lbm_mlp_last_error",
+    "lbm_mlp_train", "lbm_mlp_last_error",
     "lbm_residual_noalloc", "lbm_check_bounded_wait", "lbm_probe_resident_wait",
     "lbm_nd_lattice_speed", "lbm_nd_create", "lbm_nd_init", "lbm_nd_step", "lbm_nd_sync",
     "lbm_nd_moments", "lbm_nd_populations", "lbm_nd_energy", "lbm_nd_step_count",
@@ -121,6 +124,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_get_side": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
         "lbm_set_graph_chunk": (st, [vp, ctypes.c_int]),
         "lbm_autotune": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
+        "lbm_set_rounding": (st, [vp, ctypes.c_int]),
         "lbm_set_staged_config": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int]),
         "lbm_get_staged_config": (st, [vp] + [ctypes.POINTER(ctypes.c_int)] * 5),
@@ -144,6 +148,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
         "lbm_batch_profiles": (st, [vp, vp]),
         "lbm_batch_init_profiles": (st, [vp, vp]),
+        "lbm_analytic_profiles": (st, [vp, ctypes.c_int, vp, ctypes.c_int, vp]),
         "lbm_mlp_create": (st, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, vp,
                                 ctypes.POINTER(vp)]),
         "lbm_mlp_destroy": (None, [vp]),
@@ -153,6 +158,8 @@ def load_library(path: str = LIB_PATH):
         "lbm_mlp_forward": (st, [vp, vp, ctypes.c_int, vp]),
         "lbm_mlp_loss_grad": (st, [vp, vp, vp, ctypes.c_int, dp, vp]),
         "lbm_mlp_train_step": (st, [vp, vp, vp, ctypes.c_int, ctypes.c_float, dp]),
+        "lbm_mlp_train": (st, [vp, vp, vp, ctypes.c_int, ctypes.c_int, c_long, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_ulonglong, vp]),
         "lbm_mlp_last_error": (ctypes.c_char_p, [vp]),
         "lbm_residual_noalloc": (st, [vp, vp, vp, vp, vp, vp, ctypes.c_longlong,
                                       ctypes.c_double, c_long, vp, dp, dp]),
@@ -239,7 +246,8 @@ class Lattice:
 
     def __init__(self, nx, ny, tau_N, tau_R, bc_x=PERIODIC, bc_y=PERIODIC, delta_e=0.0,
                  precision="fp32", e_ref=1.0, kernel="auto", device=None,
-                 torch_buffers=True, graph_chunk=None, sides=None, buffers=None):
+                 torch_buffers=True, graph_chunk=None, sides=None, buffers=None,
+                 rounding="nearest"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the phonon LBM runs only on the GPU")
@@ -287,6 +295,12 @@ class Lattice:
             self.set_kernel(kernel)
         if graph_chunk is not None:
             self._check(self._lib.lbm_set_graph_chunk(self._ctx, int(graph_chunk)))
+        if rounding != "nearest":
+            self.set_rounding(rounding)
+
+    def set_rounding(self, rounding: str):
+        """lbm_set_rounding: "nearest" or "stochastic" (16-bit storage)."""
+        self._check(self._lib.lbm_set_rounding(self._ctx, ROUNDINGS[rounding]))
 
     # -- plumbing -----------------------------------------------------------
     def _check(self, st):
@@ -472,6 +486,37 @@ class Lattice:
         return 2.0 * nbytes / (self.nx * self.ny)
 
 
+def _instances(instances):
+    """ctypes array of lbm_instance from dicts (nx, ny, tau_N, tau_R and
+    optional bc_x, bc_y, delta_e)."""
+    arr = (Instance * len(instances))()
+    for a, i in zip(arr, instances):
+        a.nx, a.ny = int(i["nx"]), int(i["ny"])
+        a.tau_N, a.tau_R = float(i["tau_N"]), float(i["tau_R"])
+        a.bc = Boundary(int(i.get("bc_x", PERIODIC)), int(i.get("bc_y", PERIODIC)),
+                        float(i.get("delta_e", 0.0)))
+    return arr
+
+
+def analytic_profiles(instances, out=None, op=0):
+    """lbm_analytic_profiles: the Eq. 68 start of each instance in the
+    layout of Batch.profiles(); op 0 returns them (a new CUDA float32
+    tensor [n, 512]), op 1 / -1 adds them to / subtracts them from `out`
+    in place."""
+    import torch
+    lib = load_library()
+    if out is None:
+        out = torch.empty((len(instances), 512), dtype=torch.float32, device="cuda")
+    assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+    assert out.shape == (len(instances), 512)
+    st = lib.lbm_analytic_profiles(_instances(instances), len(instances),
+                                   ctypes.c_void_p(out.data_ptr()), int(op),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != OK:
+        raise LBMError(st, lib.lbm_last_error(None).decode())
+    return out
+
+
 class Batch:
     """Many independent lattices advanced by one launch per step (see the
     batched solver in include/phonon_lbm.h).  ``instances`` is a list of
@@ -484,12 +529,7 @@ class Batch:
         self._lib = load_library()
         self.torch = torch
         self.instances = [dict(i) for i in instances]
-        arr = (Instance * len(instances))()
-        for a, i in zip(arr, self.instances):
-            a.nx, a.ny = int(i["nx"]), int(i["ny"])
-            a.tau_N, a.tau_R = float(i["tau_N"]), float(i["tau_R"])
-            a.bc = Boundary(int(i.get("bc_x", PERIODIC)), int(i.get("bc_y", PERIODIC)),
-                            float(i.get("delta_e", 0.0)))
+        arr = _instances(self.instances)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.stream = torch.cuda.current_stream()
         self._b = ctypes.c_void_p()
@@ -679,6 +719,18 @@ class Mlp:
                                                  ctypes.c_void_p(t.data_ptr()), x.shape[0],
                                                  ctypes.c_float(lr), ctypes.byref(loss)))
         return loss.value
+
+    def train(self, x, t, steps, batch, lr, lr_final, seed=0):
+        """lbm_mlp_train: `steps` Adam steps on minibatches of the rows of
+        (x, t) drawn on the device, one captured step replayed; returns the
+        per-step losses (numpy float32)."""
+        x, t = self._dev(x), self._dev(t)
+        hist = np.empty(int(steps), dtype=np.float32)
+        self._check(self._lib.lbm_mlp_train(
+            self._m, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()), x.shape[0],
+            int(batch), int(steps), ctypes.c_float(lr), ctypes.c_float(lr_final),
+            ctypes.c_ulonglong(seed), hist.ctypes.data_as(ctypes.c_void_p)))
+        return hist
 
 
 class LatticeND:

@@ -149,8 +149,10 @@ batch_finalize(const double *__restrict__ partials, const Range *__restrict__ ra
 // (device doubles [ny][nx]): for output point j of P = 256 at Y = j/(P-1),
 // linear interpolation between rows y0 and y0 + 1 of the row means of
 //   Q = q_x nx / ((5/9) tau_R delta_e)     (heat flux over the Fourier flux)
-//   E = (e + delta_e (x - (nx-1)/2) / nx - e_ref) / delta_e   (e minus its
-//        x-affine part).
+//   E = (e + delta_e (x - (nx-1)/2) / nx - e_ref) nx / delta_e   (e minus
+//        its x-affine part, in units of the drop per cell delta_e / nx).
+// Both are set by the temperature gradient alone, so a channel's profile
+// does not depend on its length.
 // One block per output point; out[0..P) = Q, out[P..2P) = E.
 constexpr int PROFILE_POINTS = 256;
 
@@ -178,7 +180,7 @@ channel_profile(const double *__restrict__ e, const double *__restrict__ qx, int
         const double q = ((1.0 - w) * res[0] + w * res[1]) / nx;
         const double ed = ((1.0 - w) * res[2] + w * res[3]) / nx;
         out[j] = (float)(q / q_unit);
-        out[PROFILE_POINTS + j] = (float)(ed / delta_e);
+        out[PROFILE_POINTS + j] = (float)(ed * nx / delta_e);
     }
 }
 
@@ -208,7 +210,7 @@ profile_e_mean(const float *__restrict__ prof, int ny, double *__restrict__ out)
 
 // Initial fields of one channel from its predicted profile (same
 // normalisation as channel_profile): q_x = Q(Y) q_unit, q_y = 0,
-// e = e_ref + delta_e (E(Y) - mean E - (x - (nx-1)/2) / nx), Y = y/(ny-1).
+// e = e_ref + (delta_e / nx) (E(Y) - mean E - (x - (nx-1)/2)), Y = y/(ny-1).
 __global__ void channel_fields(const float *__restrict__ prof, int nx, int ny, double e_ref,
                                double delta_e, double q_unit, const double *__restrict__ e_mean,
                                double *__restrict__ e, double *__restrict__ qx,
@@ -219,10 +221,17 @@ __global__ void channel_fields(const float *__restrict__ prof, int nx, int ny, d
         const int y = (int)(node / nx), x = (int)(node - (long long)y * nx);
         const double Q = profile_at(prof, y, ny);
         const double E = profile_at(prof + PROFILE_POINTS, y, ny) - *e_mean;
-        e[node] = e_ref + delta_e * (E - ((double)x - 0.5 * (nx - 1)) / nx);
+        e[node] = e_ref + delta_e / nx * (E - ((double)x - 0.5 * (nx - 1)));
         qx[node] = Q * q_unit;
         qy[node] = 0.0;
     }
+}
+
+// out[i] += a v[i]
+__global__ void add_scaled(float *__restrict__ out, const float *__restrict__ v, float a,
+                           long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = out[i] + a * v[i];
 }
 
 }  // namespace
@@ -1056,6 +1065,69 @@ lbm_status lbm_batch_profiles(lbm_batch *b, float *out) {
         BCK(b, cudaGetLastError());
     }
     BCK(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+// Eq. 68: the heat flux across a channel of width d between diffuse walls
+// under a uniform temperature gradient, over the Fourier flux, from the
+// phonon hydrodynamic model with the slip condition of Eq. 11, at Y = y/d:
+//   Q(Y) = 1 - (exp((Y - 1)/Kn_eff) + exp(-Y/Kn_eff)) /
+//              (1 + exp(-1/Kn_eff) + (8/15)(Kn_C/Kn_eff)(1 - exp(-1/Kn_eff))),
+// Kn_eff = sqrt(tau_C tau_R v_g^2 / 5) / d, Kn_C = v_g tau_C / d.  In lattice
+// units v_g = sqrt(5/3) and tau_C = 1 / (1/tau_N + 1/tau_R) (Section 2.1).
+static double eq68_flux(double Y, double tau_N, double tau_R, double d) {
+    const double tau_C = 1.0 / ((std::isinf(tau_N) ? 0.0 : 1.0 / tau_N) + 1.0 / tau_R);
+    const double vg2 = 5.0 / 3.0;
+    const double kn_eff = std::sqrt(tau_C * tau_R * vg2 / 5.0) / d;
+    const double kn_c = std::sqrt(vg2) * tau_C / d;
+    const double a = std::exp(-1.0 / kn_eff);
+    const double num = std::exp((Y - 1.0) / kn_eff) + std::exp(-Y / kn_eff);
+    const double den = 1.0 + a + (8.0 / 15.0) * (kn_c / kn_eff) * (1.0 - a);
+    return 1.0 - num / den;
+}
+
+lbm_status lbm_analytic_profiles(const lbm_instance *inst, int count, float *out, int op,
+                                 void *stream) {
+    if (!inst || !out || count < 1) return bfail(nullptr, LBM_EINVAL, "bad arguments");
+    if (op < -1 || op > 1) return bfail(nullptr, LBM_EINVAL, "op must be -1, 0 or 1");
+    for (int i = 0; i < count; ++i) {
+        const lbm_instance &in = inst[i];
+        if (in.bc.y != LBM_BC_DIFFUSE_WALLS || in.ny < 2 || !std::isfinite(in.tau_R) ||
+            !(in.tau_R > 0.0) || !(in.tau_N > 0.0))
+            return bfail(nullptr, LBM_EUNSUPPORTED,
+                         "instance " + std::to_string(i) +
+                             ": the analytic profile needs walls on y, ny >= 2 and finite "
+                             "tau_R");
+    }
+    std::vector<float> prof((size_t)count * 2 * PROFILE_POINTS, 0.f);
+    for (int i = 0; i < count; ++i) {
+        const lbm_instance &in = inst[i];
+        const double d = in.ny - 1;       // the walls sit on rows 0 and ny - 1
+        float *p = prof.data() + (size_t)i * 2 * PROFILE_POINTS;
+        for (int j = 0; j < PROFILE_POINTS; ++j)
+            p[j] = (float)eq68_flux((double)j / (PROFILE_POINTS - 1), in.tau_N, in.tau_R, d);
+        // E(Y) = 0: e affine in x with the steady slope, uniform across
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = prof.size();
+    cudaError_t e = cudaSuccess;
+    if (op == 0) {
+        e = cudaMemcpyAsync(out, prof.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    } else {
+        float *tmp = nullptr;
+        e = cudaMalloc(&tmp, sizeof(float) * n);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tmp, prof.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            add_scaled<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, tmp, (float)op,
+                                                                  (long long)n);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(tmp);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bcuda(nullptr, e, "lbm_analytic_profiles");
     return LBM_OK;
 }
 

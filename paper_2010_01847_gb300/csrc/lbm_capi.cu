@@ -25,6 +25,7 @@ struct lbm_ctx {
     double side_val[4] = {0.0, 0.0, 0.0, 0.0};
     double tau_N = 0.0, tau_R = 0.0, tau = 0.0, tau_r = 0.0, kappa = 1.0, sigma = 0.0;
     int precision = 0;
+    int rounding = LBM_ROUND_NEAREST;   // 16-bit storage only
     double e_ref = 1.0;
     double scale = 1.0;
     cudaStream_t stream = nullptr;
@@ -138,6 +139,7 @@ Coef<C> make_coef(const lbm_ctx *c) {
         k.side_flux[sd] = (C)(kind == LBM_SIDE_HEAT_FLUX ? c->scale * v / c->kappa : 0.0);
     }
     set_tile_refs(k, c->precision, c->nx, c->ny, c->tau, c->tau_r);
+    k.stochastic = c->rounding == LBM_ROUND_STOCHASTIC ? 1 : 0;
     return k;
 }
 
@@ -834,6 +836,20 @@ lbm_status lbm_set_kernel(lbm_ctx *c, int kernel) {
 }
 
 int lbm_get_kernel(const lbm_ctx *c) { return c ? c->kernel : -1; }
+
+lbm_status lbm_set_rounding(lbm_ctx *c, int rounding) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (rounding != LBM_ROUND_NEAREST && rounding != LBM_ROUND_STOCHASTIC)
+        return fail(c, LBM_EINVAL, "unknown rounding");
+    if (!has_tile_refs(c->precision) && rounding != LBM_ROUND_NEAREST)
+        return fail(c, LBM_EUNSUPPORTED, "stochastic rounding applies to 16-bit storage");
+    if (rounding != c->rounding) {
+        DeviceGuard g(c->device);
+        drop_graphs(c);       // their launches hold the rounding
+        c->rounding = rounding;
+    }
+    return LBM_OK;
+}
 
 lbm_status lbm_set_side(lbm_ctx *c, int side, int kind, double value) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");

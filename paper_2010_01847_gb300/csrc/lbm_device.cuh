@@ -58,6 +58,7 @@ struct Coef {
     C rh_axis, rh_diag;
     C ref_rho;                // 1 / (4 nodes-per-tile): tile sum of rho -> reference
     C ref_gamma;              // gamma / (4 nodes-per-tile), gamma m = post-collision flux
+    int stochastic;           // 16-bit storage rounded stochastically (refs16.cuh)
 };
 
 // Storage traits: how a population plane element is stored and converted.

@@ -45,17 +45,20 @@ __device__ __forceinline__ float gelu_grad(float x) {
     return cdf + x * pdf;
 }
 
-enum { EPI_NONE = 0, EPI_GELU = 1 };
+enum { EPI_NONE = 0, EPI_GELU = 1, EPI_GELU_BWD = 2 };
 
 // C[m, n] = sum_k A(m, k) B(k, n) (+ bias[n]) with A(m, k) = A[m*am + k*ak],
 // B(k, n) = B[k*bk + n*bn] (any strides: every transposition the forward and
 // backward passes need).  Outputs (each optional): pre = the FP32 result,
 // out = the FP32 result after the epilogue, outb = the same in BF16.
+// Epilogues: GELU (forward), GELU backward (the result times GELU'(aux[m, n]),
+// aux the pre-activation of the layer below: dZ = dX (.) GELU'(Z)).
 __global__ void __launch_bounds__(GEMM_THREADS)
 gemm_bf16(const __nv_bfloat16 *__restrict__ A, long long am, long long ak,
           const __nv_bfloat16 *__restrict__ B, long long bk, long long bn,
           const float *__restrict__ bias, int M, int N, int K, int epi,
-          float *__restrict__ pre, float *__restrict__ out, __nv_bfloat16 *__restrict__ outb) {
+          const float *__restrict__ aux, float *__restrict__ pre, float *__restrict__ out,
+          __nv_bfloat16 *__restrict__ outb) {
     __shared__ __nv_bfloat16 As[TM][TK + 8];
     __shared__ __nv_bfloat16 Bs[TN][TK + 8];     // stored [n][k]
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
@@ -113,6 +116,7 @@ gemm_bf16(const __nv_bfloat16 *__restrict__ A, long long am, long long ak,
                 const long long o = (long long)m * N + n;
                 if (pre) pre[o] = v;
                 if (epi == EPI_GELU) v = gelu(v);
+                if (epi == EPI_GELU_BWD) v = v * gelu_grad(aux[o]);
                 if (out) out[o] = v;
                 if (outb) outb[o] = __float2bfloat16_rn(v);
             }
@@ -141,24 +145,29 @@ __global__ void mse_grad(const float *__restrict__ y, const float *__restrict__ 
     block_sum5_store(acc, loss_partials + (size_t)blockIdx.x * 5);
 }
 
-// dZ = dX (.) GELU'(pre), in place on the FP32 gradient, plus a BF16 copy.
-__global__ void gelu_backward(float *__restrict__ g, const float *__restrict__ pre, long long n,
-                              __nv_bfloat16 *__restrict__ gb) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float v = g[i] * gelu_grad(pre[i]);
-        g[i] = v;
-        gb[i] = __float2bfloat16_rn(v);
-    }
-}
-
-// db[n] = sum over the batch of dZ[b, n] (one thread per n, fixed order).
-__global__ void bias_grad(const float *__restrict__ dz, int B, int N, float *__restrict__ db) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+// db[n] = sum over the batch of dZ[b, n]: a block of 8 warps per 32
+// columns, warp w summing rows w, w + 8, ... (lanes on consecutive columns,
+// loads independent of the running sums), then the 8 warp sums added in
+// warp order: a fixed order, so the result does not vary between runs.
+constexpr int BIAS_WARPS = 8;
+__global__ void __launch_bounds__(32 * BIAS_WARPS)
+bias_grad(const float *__restrict__ dz, int B, int N, float *__restrict__ db) {
+    __shared__ float part[BIAS_WARPS][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int b = 0; b < B; ++b) s += dz[(long long)b * N + n];
-    db[n] = s;
+    if (n < N) {
+#pragma unroll 8
+        for (int b = warp; b < B; b += BIAS_WARPS) s += dz[(long long)b * N + n];
+    }
+    part[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && n < N) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < BIAS_WARPS; ++w) t += part[w][lane];
+        db[n] = t;
+    }
 }
 
 // Adam on the flat FP32 parameters, refreshing the BF16 copy of every weight.
@@ -166,6 +175,83 @@ __global__ void adam(float *__restrict__ p, const float *__restrict__ g, float *
                      float *__restrict__ v, long long n, float lr, float b1, float b2, float eps,
                      float c1, float c2, const long long *__restrict__ wmap,
                      __nv_bfloat16 *__restrict__ pb) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float w = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = w;
+        if (wmap[i] >= 0) pb[wmap[i]] = __float2bfloat16_rn(w);
+    }
+}
+
+// Per-step scalars of the device training loop (train_setup writes them).
+struct TrainState {
+    long long t;          // Adam steps taken so far (all calls)
+    long long local;      // steps of this call so far
+    long long cur;        // the step being run (this call's numbering)
+    float lr, c1, c2;     // learning rate and bias corrections of the step
+};
+
+// One thread: the step's learning rate (cosine from lr to lr_final over
+// `steps`) and Adam's bias corrections 1 - beta^t, then the counters.
+__global__ void train_setup(TrainState *st, long long steps, float lr, float lr_final,
+                            float b1, float b2) {
+    const long long t = st->t + 1, s = st->local;
+    st->cur = s;
+    st->lr = (float)((double)lr_final +
+                     0.5 * ((double)lr - (double)lr_final) *
+                         (1.0 + cos(3.14159265358979323846 * (double)s / (double)steps)));
+    st->c1 = 1.f - (float)pow((double)b1, (double)t);     // as lbm_mlp_train_step forms them
+    st->c2 = 1.f - (float)pow((double)b2, (double)t);
+    st->t = t;
+    st->local = s + 1;
+}
+
+// SplitMix64 (Steele, Lea and Flood's generator) of a 64-bit counter.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// The step's minibatch: row j is sample (batch >= n ? j : SplitMix64(seed ^
+// (step batch + j)) mod n), drawn with replacement; rows of x [n x kx] and
+// t [n x kt] are copied to xb and tb.
+__global__ void gather_rows(const float *__restrict__ x, const float *__restrict__ t, int n,
+                            int kx, int kt, int batch, unsigned long long seed,
+                            const TrainState *__restrict__ st, float *__restrict__ xb,
+                            float *__restrict__ tb) {
+    const int kw = kx > kt ? kx : kt;
+    const long long total = (long long)batch * kw;
+    const unsigned long long base = (unsigned long long)st->cur * (unsigned long long)batch;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(i / kw), c = (int)(i - (long long)j * kw);
+        const long long src = batch >= n ? j
+                                         : (long long)(splitmix64(seed ^ (base + (unsigned)j)) %
+                                                       (unsigned long long)n);
+        if (c < kx) xb[(long long)j * kx + c] = x[src * kx + c];
+        if (c < kt) tb[(long long)j * kt + c] = t[src * kt + c];
+    }
+}
+
+// The step's loss (mean of the squared errors) into the history.
+__global__ void record_loss(const double *__restrict__ total, double inv_n,
+                            const TrainState *__restrict__ st, float *__restrict__ hist) {
+    hist[st->cur] = (float)(*total * inv_n);
+}
+
+// Adam with the step's scalars from the device (the training loop).
+__global__ void adam_dev(float *__restrict__ p, const float *__restrict__ g,
+                         float *__restrict__ m, float *__restrict__ v, long long n, float b1,
+                         float b2, float eps, const TrainState *__restrict__ st,
+                         const long long *__restrict__ wmap, __nv_bfloat16 *__restrict__ pb) {
+    const float lr = st->lr, c1 = st->c1, c2 = st->c2;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -205,7 +291,11 @@ struct lbm_mlp {
     std::vector<float *> act;             // FP32 outputs per layer
     std::vector<__nv_bfloat16 *> actb;    // BF16 layer inputs: actb[0] = X, actb[l+1] = out of l
     float *g0 = nullptr, *g1 = nullptr;   // gradient ping-pong [B x max width]
-    __nv_bfloat16 *gb = nullptr;
+    __nv_bfloat16 *gb = nullptr, *gb1 = nullptr;   // BF16 copies of the two
+    // device training loop: state, gathered minibatch, capture stream
+    TrainState *tstate = nullptr;
+    float *xb = nullptr, *tb = nullptr;
+    cudaStream_t cap = nullptr;
     double *loss_part = nullptr;
     long long steps = 0;
     std::string err;
@@ -233,17 +323,17 @@ lbm_status mcuda(lbm_mlp *m, cudaError_t e, const char *where) {
 
 cudaError_t gemm(cudaStream_t s, const __nv_bfloat16 *A, long long am, long long ak,
                  const __nv_bfloat16 *B, long long bk, long long bn, const float *bias, int M,
-                 int N, int K, int epi, float *pre, float *out, __nv_bfloat16 *outb) {
+                 int N, int K, int epi, const float *aux, float *pre, float *out,
+                 __nv_bfloat16 *outb) {
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-    gemm_bf16<<<grid, GEMM_THREADS, 0, s>>>(A, am, ak, B, bk, bn, bias, M, N, K, epi, pre, out,
-                                            outb);
+    gemm_bf16<<<grid, GEMM_THREADS, 0, s>>>(A, am, ak, B, bk, bn, bias, M, N, K, epi, aux, pre,
+                                            out, outb);
     return cudaGetLastError();
 }
 
-// Forward pass of `batch` rows of X (FP32 device [batch x K_0]); the output
-// layer's FP32 result is act[L-1].
-cudaError_t forward(lbm_mlp *m, const float *x, int batch) {
-    cudaStream_t s = m->stream;
+// Forward pass of `batch` rows of X (FP32 device [batch x K_0]) on stream
+// s; the output layer's FP32 result is act[L-1].
+cudaError_t forward(lbm_mlp *m, const float *x, int batch, cudaStream_t s) {
     to_bf16<<<grid1((long long)batch * m->widths[0]), 256, 0, s>>>(
         x, m->actb[0], (long long)batch * m->widths[0]);
     cudaError_t e = cudaGetLastError();
@@ -251,8 +341,41 @@ cudaError_t forward(lbm_mlp *m, const float *x, int batch) {
         const int K = m->widths[l], N = m->widths[l + 1];
         const bool last = l == m->layers - 1;
         e = gemm(s, m->actb[l], K, 1, m->wb + m->wb_off[l], 1, K, m->params + m->b_off[l], batch,
-                 N, K, last ? EPI_NONE : EPI_GELU, m->pre[l], m->act[l],
+                 N, K, last ? EPI_NONE : EPI_GELU, nullptr, m->pre[l], m->act[l],
                  last ? nullptr : m->actb[l + 1]);
+    }
+    return e;
+}
+
+// Loss partial sums and every parameter's gradient (into m->grads) for
+// targets t of the rows forward() last ran, on stream s; no host copy, no
+// synchronisation.  The total loss (sum of squares) lands at
+// loss_part[5 * 4096].
+cudaError_t backward(lbm_mlp *m, const float *t, int batch, cudaStream_t s) {
+    const int L = m->layers;
+    const long long no = (long long)batch * m->widths[L];
+    const unsigned gl = grid1(no);
+    mse_grad<<<gl, 256, 0, s>>>(m->act[L - 1], t, no, 1.0f / (float)no, m->g0, m->gb,
+                                m->loss_part);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_finalize(m->loss_part, (int)gl, m->loss_part + 5 * 4096, s);
+    float *g = m->g0, *gn = m->g1;
+    __nv_bfloat16 *gbf = m->gb, *gbn = m->gb1;
+    for (int l = L - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int K = m->widths[l], N = m->widths[l + 1];
+        // dW_l = dZ_l^T X_l   ([N x K], sum over the batch)
+        e = gemm(s, gbf, 1, N, m->actb[l], K, 1, nullptr, N, K, batch, EPI_NONE, nullptr,
+                 nullptr, m->grads + m->w_off[l], nullptr);
+        if (e != cudaSuccess) break;
+        bias_grad<<<(N + 31) / 32, 32 * BIAS_WARPS, 0, s>>>(g, batch, N, m->grads + m->b_off[l]);
+        e = cudaGetLastError();
+        if (l == 0 || e != cudaSuccess) break;
+        // dZ_{l-1} = (dZ_l W_l) (.) GELU'(Z_{l-1})   ([B x K], the GELU of
+        // layer l - 1 in the product's epilogue)
+        e = gemm(s, gbf, N, 1, m->wb + m->wb_off[l], K, 1, nullptr, batch, K, N, EPI_GELU_BWD,
+                 m->pre[l - 1], nullptr, gn, gbn);
+        std::swap(g, gn);
+        std::swap(gbf, gbn);
     }
     return e;
 }
@@ -309,6 +432,7 @@ lbm_status lbm_mlp_create(const int *widths, int n_widths, int max_batch, void *
     al((void **)&m->g0, sizeof(float) * (size_t)max_batch * wmax);
     al((void **)&m->g1, sizeof(float) * (size_t)max_batch * wmax);
     al((void **)&m->gb, sizeof(__nv_bfloat16) * (size_t)max_batch * wmax);
+    al((void **)&m->gb1, sizeof(__nv_bfloat16) * (size_t)max_batch * wmax);
     al((void **)&m->loss_part, sizeof(double) * 5 * 4097);   // partials + total
     if (e == cudaSuccess) {
         std::vector<long long> map(m->n_params, -1);
@@ -347,7 +471,12 @@ void lbm_mlp_destroy(lbm_mlp *m) {
     cudaFree(m->g0);
     cudaFree(m->g1);
     cudaFree(m->gb);
+    cudaFree(m->gb1);
     cudaFree(m->loss_part);
+    cudaFree(m->tstate);
+    cudaFree(m->xb);
+    cudaFree(m->tb);
+    if (m->cap) cudaStreamDestroy(m->cap);
     delete m;
 }
 
@@ -382,7 +511,7 @@ lbm_status lbm_mlp_forward(lbm_mlp *m, const float *x, int batch, float *y) {
     NvtxRange nvtx_("lbm_mlp_forward");
     if (!m || !x || !y) return mfail(m, LBM_EINVAL, "NULL argument");
     if (batch < 1 || batch > m->max_batch) return mfail(m, LBM_EINVAL, "batch out of range");
-    MCK(m, forward(m, x, batch));
+    MCK(m, forward(m, x, batch, m->stream));
     MCK(m, cudaMemcpyAsync(y, m->act[m->layers - 1],
                            sizeof(float) * (size_t)batch * m->widths[m->layers],
                            cudaMemcpyDeviceToDevice, m->stream));
@@ -394,31 +523,9 @@ lbm_status lbm_mlp_forward(lbm_mlp *m, const float *x, int batch, float *y) {
 static lbm_status loss_and_grad(lbm_mlp *m, const float *x, const float *t, int batch,
                                 double *loss, float *grads_host) {
     cudaStream_t s = m->stream;
-    MCK(m, forward(m, x, batch));
-    const int L = m->layers;
-    const long long no = (long long)batch * m->widths[L];
-    const unsigned gl = grid1(no);
-    mse_grad<<<gl, 256, 0, s>>>(m->act[L - 1], t, no, 1.0f / (float)no, m->g0, m->gb,
-                                m->loss_part);
-    MCK(m, cudaGetLastError());
-    MCK(m, launch_finalize(m->loss_part, (int)gl, m->loss_part + 5 * 4096, s));
-    float *g = m->g0, *gn = m->g1;
-    for (int l = L - 1; l >= 0; --l) {
-        const int K = m->widths[l], N = m->widths[l + 1];
-        // dW_l = dZ_l^T X_l   ([N x K], sum over the batch)
-        MCK(m, gemm(s, m->gb, 1, N, m->actb[l], K, 1, nullptr, N, K, batch, EPI_NONE, nullptr,
-                    m->grads + m->w_off[l], nullptr));
-        bias_grad<<<(N + 255) / 256, 256, 0, s>>>(g, batch, N, m->grads + m->b_off[l]);
-        MCK(m, cudaGetLastError());
-        if (l == 0) break;
-        // dX_l = dZ_l W_l  ([B x K]); then through the GELU of layer l-1
-        MCK(m, gemm(s, m->gb, N, 1, m->wb + m->wb_off[l], K, 1, nullptr, batch, K, N, EPI_NONE,
-                    nullptr, gn, nullptr));
-        gelu_backward<<<grid1((long long)batch * K), 256, 0, s>>>(gn, m->pre[l - 1],
-                                                                 (long long)batch * K, m->gb);
-        MCK(m, cudaGetLastError());
-        std::swap(g, gn);
-    }
+    MCK(m, forward(m, x, batch, s));
+    MCK(m, backward(m, t, batch, s));
+    const long long no = (long long)batch * m->widths[m->layers];
     double hl = 0.0;
     MCK(m, cudaMemcpyAsync(&hl, m->loss_part + 5 * 4096, sizeof(double), cudaMemcpyDeviceToHost,
                            s));
@@ -451,6 +558,76 @@ lbm_status lbm_mlp_train_step(lbm_mlp *m, const float *x, const float *t, int ba
     adam<<<grid1(m->n_params), 256, 0, m->stream>>>(m->params, m->grads, m->m, m->v, m->n_params,
                                                     lr, b1, b2, 1e-8f, c1, c2, m->wmap, m->wb);
     MCK(m, cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_mlp_train(lbm_mlp *m, const float *x, const float *t, int n, int batch,
+                         long steps, float lr, float lr_final, unsigned long long seed,
+                         float *loss_host) {
+    NvtxRange nvtx_("lbm_mlp_train");
+    if (!m || !x || !t) return mfail(m, LBM_EINVAL, "NULL argument");
+    if (n < 1) return mfail(m, LBM_EINVAL, "n must be >= 1");
+    if (batch < 1 || batch > m->max_batch) return mfail(m, LBM_EINVAL, "batch out of range");
+    if (steps < 0) return mfail(m, LBM_EINVAL, "steps must be >= 0");
+    if (!(lr > 0.f) || !(lr_final > 0.f)) return mfail(m, LBM_EINVAL, "learning rates must be > 0");
+    if (steps == 0) return LBM_OK;
+    const int L = m->layers, kx = m->widths[0], kt = m->widths[L];
+    if (!m->tstate) {
+        MCK(m, cudaMalloc(&m->tstate, sizeof(TrainState)));
+        MCK(m, cudaMalloc(&m->xb, sizeof(float) * (size_t)m->max_batch * kx));
+        MCK(m, cudaMalloc(&m->tb, sizeof(float) * (size_t)m->max_batch * kt));
+        MCK(m, cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+    }
+    TrainState st0{m->steps, 0, 0, 0.f, 0.f, 0.f};
+    float *hist = nullptr;
+    MCK(m, cudaMalloc(&hist, sizeof(float) * (size_t)steps));
+    cudaError_t e = cudaMemcpyAsync(m->tstate, &st0, sizeof(st0), cudaMemcpyHostToDevice,
+                                    m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    // one Adam step, captured once and replayed: every per-step value (the
+    // minibatch, the learning rate, the bias corrections) comes from the
+    // device state, so the graph is the same for every step
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    const float b1 = 0.9f, b2 = 0.999f;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaStream_t s = m->cap;
+        cudaError_t le;
+        train_setup<<<1, 1, 0, s>>>(m->tstate, (long long)steps, lr, lr_final, b1, b2);
+        le = cudaGetLastError();
+        if (le == cudaSuccess) {
+            gather_rows<<<grid1((long long)batch * (kx > kt ? kx : kt)), 256, 0, s>>>(
+                x, t, n, kx, kt, batch, seed, m->tstate, m->xb, m->tb);
+            le = cudaGetLastError();
+        }
+        if (le == cudaSuccess) le = forward(m, m->xb, batch, s);
+        if (le == cudaSuccess) le = backward(m, m->tb, batch, s);
+        if (le == cudaSuccess) {
+            record_loss<<<1, 1, 0, s>>>(m->loss_part + 5 * 4096,
+                                        1.0 / ((double)batch * kt), m->tstate, hist);
+            le = cudaGetLastError();
+        }
+        if (le == cudaSuccess) {
+            adam_dev<<<grid1(m->n_params), 256, 0, s>>>(m->params, m->grads, m->m, m->v,
+                                                        m->n_params, b1, b2, 1e-8f, m->tstate,
+                                                        m->wmap, m->wb);
+            le = cudaGetLastError();
+        }
+        e = cudaStreamEndCapture(s, &g);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    for (long i = 0; i < steps && e == cudaSuccess; ++i) e = cudaGraphLaunch(ge, m->stream);
+    if (e == cudaSuccess && loss_host)
+        e = cudaMemcpyAsync(loss_host, hist, sizeof(float) * (size_t)steps,
+                            cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaFree(hist);
+    if (e != cudaSuccess) return mcuda(m, e, "lbm_mlp_train");
+    m->steps += steps;
     return LBM_OK;
 }
 

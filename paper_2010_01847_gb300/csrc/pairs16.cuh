@@ -68,13 +68,14 @@ struct NoPairHook {
 // for the next step's readers), and the tile's sums of rho, m_x, m_y
 // (moments_f32, tree order of tile_tree_pairs) come back in sums.
 // hook(m, f) sees each pair's pulled state (after the walls, before the
-// collision).
-template <typename T, typename Hook = NoPairHook>
+// collision).  SR: stochastic rounding of the stored values (refs16.cuh),
+// pair0 the global index of the thread's first node pair.
+template <typename T, bool SR = false, typename Hook = NoPairHook>
 __device__ __forceinline__ void collide_words16(uint4 (&w)[8], const Coef<float> &k,
                                                 const SeamAdd &seam, bool bottom, bool top,
                                                 const float (&Rd)[8], const float (&Rx)[8],
                                                 const float (&Re)[8], float (&sums)[3],
-                                                const Hook &hook = Hook()) {
+                                                unsigned pair0 = 0u, const Hook &hook = Hook()) {
     float2 r01, x01, y01, r23, x23, y23;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -112,7 +113,8 @@ __device__ __forceinline__ void collide_words16(uint4 (&w)[8], const Coef<float>
         relax_f32(f, rho, mx, my, k);
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-            set_word(w[i], m, f2_to_word<T>(f_sub(f[i], make_float2(Re[i], Re[i]))));
+            set_word(w[i], m,
+                     store_word<T, SR>(f_sub(f[i], make_float2(Re[i], Re[i])), pair0 + m, i));
     }
     sums[0] = tile_tree_pairs(r01, r23);
     sums[1] = tile_tree_pairs(x01, x23);

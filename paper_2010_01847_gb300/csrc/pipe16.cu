@@ -96,7 +96,7 @@ __device__ __forceinline__ VPos vpos(long long t, long long total, int tpr, int 
 #define PLBM_P16_BLOCKS 2
 #endif
 
-template <typename T>
+template <typename T, bool SR>
 __global__ void __launch_bounds__(THREADS, PLBM_P16_BLOCKS)
 step_pipe16(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long long plane,
             int bc_x, int bc_y, Coef<float> k) {
@@ -231,8 +231,9 @@ step_pipe16(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long
             float sums[3];
             float Re[8];
             ref_pops(ref_of<T>(enc), k, Re);
-            collide_words16<T>(w, k, seam, cur.bottom, cur.top, Rd, Rx, Re, sums);
             const long long out = (long long)cur.y * nx + cur.x0;
+            collide_words16<T, SR>(w, k, seam, cur.bottom, cur.top, Rd, Rx, Re, sums,
+                                   (unsigned)(out >> 1));
 #pragma unroll
             for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, w[i]);
             st_ref(dst, k, t, enc, next_ref<T>(sums[0], sums[1], sums[2], k, k.ref_gamma));
@@ -249,21 +250,22 @@ struct Prep {
     bool ready = false;
     int grid = 0;
 };
-Prep g_prep[64][2];
+Prep g_prep[64][2][2];      // device, storage kind, rounding
 
 template <typename T> constexpr int kind_of() { return std::is_same<T, __half>::value ? 0 : 1; }
 
-template <typename T>
+template <typename T, bool SR>
 cudaError_t prepare_t(int dev) {
-    Prep &p = g_prep[dev][kind_of<T>()];
+    Prep &p = g_prep[dev][kind_of<T>()][SR ? 1 : 0];
     if (p.ready) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(step_pipe16<T>,
+    cudaError_t e = cudaFuncSetAttribute(step_pipe16<T, SR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
     int sms = 0, per_sm = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_pipe16<T>, THREADS, SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_pipe16<T, SR>, THREADS,
+                                                      SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     p.grid = sms * per_sm;
@@ -278,8 +280,14 @@ cudaError_t prepare_pipe16(int precision) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (precision == PREC_FP16) return prepare_t<__half>(dev);
-    if (precision == PREC_BF16) return prepare_t<__nv_bfloat16>(dev);
+    if (precision == PREC_FP16) {
+        if ((e = prepare_t<__half, false>(dev)) != cudaSuccess) return e;
+        return prepare_t<__half, true>(dev);
+    }
+    if (precision == PREC_BF16) {
+        if ((e = prepare_t<__nv_bfloat16, false>(dev)) != cudaSuccess) return e;
+        return prepare_t<__nv_bfloat16, true>(dev);
+    }
     return cudaErrorInvalidValue;
 }
 
@@ -290,12 +298,17 @@ cudaError_t launch_step_pipe16(const T *src, T *dst, int nx, int ny, int bc_x, i
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    const Prep &p = g_prep[dev][kind_of<T>()];
+    const bool sr = k.stochastic != 0;
+    const Prep &p = g_prep[dev][kind_of<T>()][sr ? 1 : 0];
     if (!p.ready) return cudaErrorNotReady;      // prepare_pipe16 was not called on this device
     const long long chunks = ((long long)(nx / 8) * ny + THREADS - 1) / THREADS;
     const int grid = (int)(chunks < p.grid ? chunks : p.grid);
-    step_pipe16<T><<<grid, THREADS, SMEM, stream>>>(src, dst, nx, ny, (long long)nx * ny, bc_x,
-                                                    bc_y, k);
+    if (sr)
+        step_pipe16<T, true><<<grid, THREADS, SMEM, stream>>>(src, dst, nx, ny,
+                                                              (long long)nx * ny, bc_x, bc_y, k);
+    else
+        step_pipe16<T, false><<<grid, THREADS, SMEM, stream>>>(src, dst, nx, ny,
+                                                               (long long)nx * ny, bc_x, bc_y, k);
     return cudaGetLastError();
 }
 

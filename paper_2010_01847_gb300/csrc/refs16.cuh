@@ -66,6 +66,53 @@ template <> __device__ __forceinline__ unsigned f2_to_word<__nv_bfloat16>(float2
     return r;
 }
 
+// Stochastic rounding, an option of 16-bit storage (round-to-nearest is the
+// default).  Round-to-nearest errors of slowly varying fields repeat step
+// after step and add up; rounding up with probability equal to the dropped
+// fraction makes each error zero on average, so they add like a random
+// walk.  The random bits are a hash of the node pair (its global index),
+// the plane and the two values' FP32 bits: deterministic, and the same in
+// every kernel that stores the pair.  FP16 drops 13 bits of an FP32
+// significand (normal range), BF16 16: those bits get a random number of
+// that width added to the magnitude, then are cut off.
+__device__ __forceinline__ unsigned sr_hash(unsigned pair, unsigned plane, unsigned a,
+                                            unsigned b) {
+    unsigned h = pair * 0x9E3779B1u ^ (plane + 1u) * 0x85EBCA77u ^ a ^ __funnelshift_l(b, b, 16);
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return h;
+}
+// One value rounded stochastically with random bits r (below the kept
+// significand), as the FP32 bit pattern of the result.
+template <int DROP>
+__device__ __forceinline__ unsigned sr_bits(float x, unsigned r) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned mag = ((b & 0x7fffffffu) + (r & ((1u << DROP) - 1u))) & ~((1u << DROP) - 1u);
+    return (b & 0x80000000u) | mag;
+}
+template <typename T> __device__ __forceinline__ unsigned f2_to_word_sr(float2 v, unsigned h);
+template <> __device__ __forceinline__ unsigned f2_to_word_sr<__half>(float2 v, unsigned h) {
+    // exact in FP16 after the cut (normal range), so the conversion keeps it
+    return f2_to_word<__half>(make_float2(__uint_as_float(sr_bits<13>(v.x, h)),
+                                          __uint_as_float(sr_bits<13>(v.y, h >> 16))));
+}
+template <> __device__ __forceinline__ unsigned f2_to_word_sr<__nv_bfloat16>(float2 v,
+                                                                             unsigned h) {
+    return (sr_bits<16>(v.x, h) >> 16) | (sr_bits<16>(v.y, h >> 16) & 0xffff0000u);
+}
+// A node pair (nodes 2 pair, 2 pair + 1 of the lattice, values v.x, v.y) of
+// plane i as a stored word, rounded as SR says.
+template <typename T, bool SR>
+__device__ __forceinline__ unsigned store_word(float2 v, unsigned pair, int i) {
+    if (SR)
+        return f2_to_word_sr<T>(v, sr_hash(pair, (unsigned)i, __float_as_uint(v.x),
+                                          __float_as_uint(v.y)));
+    return f2_to_word<T>(v);
+}
+
 // One tile's reference {rho, jx, jy} / 4 in FP32.
 struct Ref3 {
     float r, x, y;

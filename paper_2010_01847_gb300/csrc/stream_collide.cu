@@ -8,6 +8,8 @@
 // (`dst`).  Layout: structure of arrays, 8 planes of ny*nx, x fastest.
 // With RES the kernel also accumulates the residual sums of the pulled state
 // (the state at step n) and writes one set of 5 partial sums per block.
+#include <type_traits>
+
 #include "lbm_kernels.h"
 #include "pairs16.cuh"
 #include "vector_pull.cuh"
@@ -47,7 +49,7 @@ step_scalar(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
 // go through shuffles, so every lane of the warp runs the step: lanes past
 // the lattice's end (whole tiles, as nx is a multiple of 8 then) work on the
 // last node and store nothing.
-template <typename T, bool RES>
+template <typename T, bool RES, bool SR>
 __global__ void __launch_bounds__(256)
 step_scalar16(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, long long plane,
               int bc_x, int bc_y, Coef<float> k, ResidualReq<float> rq) {
@@ -69,10 +71,19 @@ step_scalar16(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny, lo
     const uint2 enc = make_uint2(both.z, both.w);
     float Re[8];
     ref_pops(ref_of<T>(enc), k, Re);
-    if (valid) {
+    // stored as node pairs (2p, 2p + 1) like the vector kernels: with
+    // stochastic rounding both lanes of a pair form the pair's random bits
+    // (lane parity = node parity: blocks hold whole warps)
+    const bool odd = node & 1;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            dst[(long long)i * plane + node] = Store<T>::put(f_sub(d[i], Re[i]));
+    for (int i = 0; i < 8; ++i) {
+        const float v = f_sub(d[i], Re[i]);
+        const float o = SR ? __shfl_xor_sync(0xffffffffu, v, 1) : 0.f;
+        const unsigned wd = store_word<T, SR>(odd ? make_float2(o, v) : make_float2(v, o),
+                                              (unsigned)(node >> 1), i);
+        if (valid)
+            reinterpret_cast<unsigned short *>(dst)[(long long)i * plane + node] =
+                (unsigned short)(odd ? wd >> 16 : wd & 0xffffu);
     }
     if (k.tile_shift == 3) {
         rho = tile_tree_lanes(rho);
@@ -110,7 +121,7 @@ template <> struct VecMinBlocks<double> { static constexpr int plain = 4, res = 
 // SIDES: the instantiation for lattices with a BC_SIDES direction (the
 // per-side treatments of Section 2.5 after the pull, as in pull_node); the
 // others never see the side logic.
-template <typename T, bool RES, bool SIDES = false>
+template <typename T, bool RES, bool SIDES = false, bool SR = false>
 __global__ void __launch_bounds__(256, RES ? VecMinBlocks<T>::res : VecMinBlocks<T>::plain)
 step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
             long long plane, int bc_x, int bc_y, Coef<typename Store<T>::C> k,
@@ -144,7 +155,7 @@ step_vector(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
         if (RES) residual_vec<C, V>(n, k, rq.inv_scale, rq.prev, plane, out, rq.have_prev != 0,
                                     loc);
         if constexpr (sizeof(T) == 2) {
-            collide_store16<T>(n, k, dst, plane, out, t, enc);     // tile t = vector t
+            collide_store16<T, SR>(n, k, dst, plane, out, t, enc);     // tile t = vector t
         } else {
 #pragma unroll
             for (int j = 0; j < V; ++j) {
@@ -195,7 +206,7 @@ __device__ __forceinline__ unsigned ld_u16(const void *p) {
 // pairs16.cuh with the tile references, residual_terms on each node in node
 // order (the history planes read and written as node pairs): the sums the
 // node-by-node kernel forms.
-template <typename T>
+template <typename T, bool SR>
 __global__ void __launch_bounds__(256, PLBM_V16_RES_BLOCKS)
 step_vector16_res(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny,
                   long long plane, int bc_x, int bc_y, Coef<float> k, ResidualReq<float> rq) {
@@ -277,7 +288,8 @@ step_vector16_res(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny
         float sums[3];
         float Re[8];
         ref_pops(ref_of<T>(enc), k, Re);
-        collide_words16<T>(w, k, seam, bottom, top, Rd, Rx, Re, sums, residual);
+        collide_words16<T, SR>(w, k, seam, bottom, top, Rd, Rx, Re, sums, (unsigned)(out >> 1),
+                               residual);
 #pragma unroll
         for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, w[i]);
         st_ref(dst, k, t, enc, next_ref<T>(sums[0], sums[1], sums[2], k, k.ref_gamma));
@@ -341,42 +353,54 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
     const unsigned blocks = (unsigned)((threads + bs - 1) / bs);
     if (blocks_out) *blocks_out = (int)blocks;
     const bool sides = bc_x == BC_SIDES || bc_y == BC_SIDES;
-    if (kernel == KERNEL_VECTOR && sides) {
-        if (rq)
-            step_vector<T, true, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
-                                                                  bc_y, k, *rq);
-        else
-            step_vector<T, false, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
-                                                                   bc_y, k, none);
-    } else if (kernel == KERNEL_VECTOR) {
-        if (rq) {
-            if constexpr (sizeof(T) == 2)
-                step_vector16_res<T><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
-                                                                bc_y, k, *rq);
+    if constexpr (sizeof(T) == 2) {
+        // 16-bit storage: the kernels of the chosen rounding (refs16.cuh)
+        auto run16 = [&](auto sr_tag) {
+            constexpr bool SR = decltype(sr_tag)::value;
+            if (kernel == KERNEL_VECTOR && sides) {
+                if (rq)
+                    step_vector<T, true, true, SR><<<blocks, bs, 0, stream>>>(
+                        src, dst, nx, ny, plane, bc_x, bc_y, k, *rq);
+                else
+                    step_vector<T, false, true, SR><<<blocks, bs, 0, stream>>>(
+                        src, dst, nx, ny, plane, bc_x, bc_y, k, none);
+            } else if (kernel == KERNEL_VECTOR) {
+                if (!rq) return launch_step_pipe16<T>(src, dst, nx, ny, bc_x, bc_y, k, stream);
+                step_vector16_res<T, SR><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane,
+                                                                    bc_x, bc_y, k, *rq);
+            } else if (rq) {
+                step_scalar16<T, true, SR><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane,
+                                                                      bc_x, bc_y, k, *rq);
+            } else {
+                step_scalar16<T, false, SR><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane,
+                                                                       bc_x, bc_y, k, none);
+            }
+            return cudaGetLastError();
+        };
+        return k.stochastic ? run16(std::true_type{}) : run16(std::false_type{});
+    } else {
+        if (kernel == KERNEL_VECTOR && sides) {
+            if (rq)
+                step_vector<T, true, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane,
+                                                                      bc_x, bc_y, k, *rq);
             else
+                step_vector<T, false, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane,
+                                                                       bc_x, bc_y, k, none);
+        } else if (kernel == KERNEL_VECTOR) {
+            if (rq)
                 step_vector<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
                                                                 bc_y, k, *rq);
-        } else {
-            if constexpr (sizeof(T) == 2)
-                return launch_step_pipe16<T>(src, dst, nx, ny, bc_x, bc_y, k, stream);
             else
                 step_vector<T, false><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
                                                                  bc_y, k, none);
+        } else {
+            if (rq)
+                step_scalar<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                                bc_y, k, *rq);
+            else
+                step_scalar<T, false><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
+                                                                 bc_y, k, none);
         }
-    } else if constexpr (sizeof(T) == 2) {
-        if (rq)
-            step_scalar16<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
-                                                              bc_y, k, *rq);
-        else
-            step_scalar16<T, false><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x,
-                                                               bc_y, k, none);
-    } else {
-        if (rq)
-            step_scalar<T, true><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
-                                                            k, *rq);
-        else
-            step_scalar<T, false><<<blocks, bs, 0, stream>>>(src, dst, nx, ny, plane, bc_x, bc_y,
-                                                             k, none);
     }
     return cudaGetLastError();
 }

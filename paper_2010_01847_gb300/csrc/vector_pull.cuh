@@ -280,7 +280,7 @@ __device__ __forceinline__ VecPos vector_local(const T *__restrict__ src, int nx
 // (boundaries applied), stores them (tile `tile` of dst, row offset `out`)
 // less the reference populations of `enc` and writes the tile's references
 // {enc, the next one from the nodes' moments} (refs16.cuh).
-template <typename T>
+template <typename T, bool SR = false>
 __device__ __forceinline__ void collide_store16(float (&n)[8][8], const Coef<float> &k,
                                                 T *__restrict__ dst, long long plane,
                                                 long long out, long long tile, uint2 enc) {
@@ -293,10 +293,13 @@ __device__ __forceinline__ void collide_store16(float (&n)[8][8], const Coef<flo
     ref_pops(ref_of<T>(enc), k, Re);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        float v[8];
+        unsigned wd[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = f_sub(n[j][i], Re[i]);
-        st_stream(dst + (long long)i * plane + out, Pack<T>::pack(v));
+        for (int m = 0; m < 4; ++m)       // node pairs (2m, 2m + 1), as the pair kernels
+            wd[m] = store_word<T, SR>(
+                make_float2(f_sub(n[2 * m][i], Re[i]), f_sub(n[2 * m + 1][i], Re[i])),
+                (unsigned)(out >> 1) + m, i);
+        st_stream(dst + (long long)i * plane + out, make_uint4(wd[0], wd[1], wd[2], wd[3]));
     }
     st_ref(dst, k, tile, enc,
            next_ref<T>(tile_tree8(rho), tile_tree8(mx), tile_tree8(my), k, k.ref_gamma));

@@ -22,6 +22,7 @@ import time
 import numpy as np
 
 from . import Batch, Mlp, inputs, tau_from_kn
+from . import analytic_profiles as _analytic
 
 WIDTHS = (3, 256, 256, 256, 256, 512)
 TRAIN_NX = 8
@@ -70,33 +71,39 @@ def steady_profiles(instances, tol=1e-8, check_every=100, max_steps=400000):
 
 
 class WarmStart:
+    """The network predicts the correction to the analytic profile (Eq. 68
+    flux, uniform energy row profile) that takes it to the scheme's own
+    steady state: the analytic part carries the physics the paper prints,
+    the network what the discrete scheme adds (the walls' slip and Knudsen
+    layers, the energy's row profile)."""
+
     def __init__(self, seed=0, max_batch=4096):
         self.net = Mlp(WIDTHS, max_batch=max_batch)
         self.net.init_params(seed)
         self.seed = seed
 
-    def train(self, x, y, steps=3000, batch=512, lr=1e-3, lr_final=1e-5):
-        """Adam on minibatches drawn with a seeded generator; cosine decay of
-        the learning rate.  Returns the loss history."""
-        rng = np.random.default_rng(self.seed + 1)
-        xd = self.net._dev(x)
-        yd = self.net._dev(y)
-        n = xd.shape[0]
-        hist = []
-        for s in range(steps):
-            idx = self.net.torch.as_tensor(rng.choice(n, size=min(batch, n), replace=False),
-                                           device="cuda")
-            lr_s = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * s / steps))
-            hist.append(self.net.train_step(xd[idx], yd[idx], lr_s))
-        return hist
+    def train(self, instances, profiles, steps=3000, batch=512, lr=1e-3, lr_final=1e-5):
+        """Fits the network to (steady profiles - analytic profiles) of the
+        training channels: Adam on minibatches drawn on the device with a
+        seeded counter-based generator, cosine decay of the learning rate
+        from lr to lr_final, all steps on the GPU (lbm_mlp_train).  Returns
+        the loss history."""
+        target = profiles.float().contiguous().clone()
+        _analytic(instances, target, op=-1)
+        return list(self.net.train(features(instances), target, steps, batch, lr, lr_final,
+                                   seed=self.seed + 1))
 
     def predict(self, instances):
-        return self.net.forward(features(instances))
+        """Profiles of the channels: the analytic ones plus the network's
+        correction (CUDA tensor [n, 512])."""
+        out = self.net.forward(features(instances)).contiguous()
+        return _analytic(instances, out, op=1)
 
 
 def solve(instances, profiles=None, tol=1e-8, check_every=100, max_steps=400000):
-    """Batched solve from the cold start (profiles None) or from predicted
-    profiles; returns (steps, final residuals, seconds, batch)."""
+    """Batched solve from the cold start (profiles None) or from profiles
+    (predicted, or analytic_profiles); returns (steps, final residuals,
+    seconds, batch)."""
     b = Batch(instances)
     if profiles is None:
         b.init()
@@ -105,3 +112,53 @@ def solve(instances, profiles=None, tol=1e-8, check_every=100, max_steps=400000)
     t0 = time.perf_counter()
     steps, r = b.solve(tol, check_every, max_steps)
     return steps, r, time.perf_counter() - t0, b
+
+
+def analytic_profiles(instances):
+    """The analytic start of every channel: Q(Y) from Eq. 68, E(Y) = 0
+    (lbm_analytic_profiles), as a CUDA tensor [n, 512]."""
+    return _analytic(instances)
+
+
+def shortened(instances, nx=TRAIN_NX):
+    """The same channels with nx columns and the same temperature gradient
+    (delta_e scaled by nx / nx_i).  A walled channel's steady state under the
+    periodic gradient is the same at every x up to the affine part of e (q
+    does not depend on x), so a short channel has the full one's steady
+    rows."""
+    return [dict(i, nx=nx, delta_e=i["delta_e"] * nx / i["nx"]) for i in instances]
+
+
+def reference_profiles(instances, tol=1e-12, check_every=500, max_steps=4000000):
+    """Steady profiles of the channels from FP64 storage solved to residual
+    < tol on their shortened copies; returns (profiles CUDA tensor [n, 512],
+    steps, residuals)."""
+    short = shortened(instances)
+    b = Batch(short, precision="fp64")
+    b.init()
+    steps, r = b.solve(tol, check_every, max_steps)
+    prof = b.profiles()
+    b.close()
+    return prof, steps, r
+
+
+def profile_errors(prof, ref, instances):
+    """Errors of end-state profiles against reference profiles (both in the
+    layout of lbm_batch_profiles, which depends on the gradient alone; ref
+    from reference_profiles).  Per channel:
+    err_q = max |Q - Q_ref| / max |Q_ref|; err_e = max over rows of the
+    difference of e's departure from its x-affine part and row mean, over
+    the largest |e - mean e| of the reference field (half the temperature
+    drop plus the largest departure).  Returns two numpy arrays."""
+    p = prof.double().cpu().numpy()
+    r = ref.double().cpu().numpy()
+    eq, ee = [], []
+    for k, i in enumerate(instances):
+        qg, qr = p[k, :256], r[k, :256]
+        eq.append(np.abs(qg - qr).max() / np.abs(qr).max())
+        drop = i["delta_e"] / i["nx"]          # both profiles: E in units of the drop per cell
+        gg = (p[k, 256:] - p[k, 256:].mean()) * drop
+        gr = (r[k, 256:] - r[k, 256:].mean()) * drop
+        span = 0.5 * abs(i["delta_e"]) * (i["nx"] - 1) / i["nx"] + np.abs(gr).max()
+        ee.append(np.abs(gg - gr).max() / span)
+    return np.array(ee), np.array(eq)

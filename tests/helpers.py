@@ -15,14 +15,14 @@ import oracle
 # metric.  1e-8 keeps a 10x margin.
 TOL = {"fp32": 1e-5, "fp16": 2e-3, "bf16": 2e-3, "fp64": 1e-8}
 
-# Sanity bounds for 16-bit storage on the short (<= 60 step) parity cases.
-# 16-bit deviation storage rounds every population every step (unit
-# roundoff u = 2^-12 for FP16, 2^-9 for BF16); on slowly varying fields
-# round-to-nearest errors repeat step after step and grow about linearly,
-# ~ steps x u (57 x u = 1.4e-2 / 0.11).  The 2e-3 gate is therefore missed
-# on longer runs; a miss is recorded as an expected failure with the
-# measured numbers, and exceeding these bounds fails.
-SANITY_16 = {"fp16": 2e-2, "bf16": 0.15}
+# BF16 keeps 8 significant bits against FP16's 11: its unit roundoff is
+# 2^-9 against 2^-12, 8 times larger.  The storage error of both is one
+# rounding per stored population and step (the arithmetic is FP32 in both),
+# so on the same case the BF16 error is about 8 times the FP16 one.  A BF16
+# result that misses the gate is an expected failure only within that
+# derived floor (8 times the FP16 error of the same case, times 1.5 for the
+# spread of rounding); beyond it, or without the FP16 comparison, it fails.
+BF16_OVER_FP16 = 8.0 * 1.5
 
 
 def err_metrics(gpu, orc):
@@ -63,17 +63,22 @@ def record_errors(precision, err_e, err_q):
                              "err_q": float(err_q)}) + "\n")
 
 
-def check_gate(precision, err_e, err_q, sanity=None):
-    """Pass within the gate; for 16-bit storage record a miss within the
-    sanity bound as xfail (with the measured errors); otherwise fail."""
+def check_gate(precision, err_e, err_q, fp16=None):
+    """Pass within the gate (FP32 1e-5, FP16 and BF16 2e-3, FP64 1e-8).  A
+    BF16 miss is recorded as an expected failure when it stays within
+    BF16_OVER_FP16 times the error of the same case with FP16 storage
+    (`fp16`: a callable returning that case's (err_e, err_q) in FP16);
+    any other miss fails."""
     import pytest
     record_errors(precision, err_e, err_q)
     tol = TOL[precision]
     if err_e <= tol and err_q <= tol:
         return
-    if precision in SANITY_16:
-        bound = SANITY_16[precision] if sanity is None else sanity
-        assert err_e <= bound and err_q <= bound, (precision, err_e, err_q)
-        pytest.xfail(f"{precision} deviation storage misses the {tol:g} gate: "
-                     f"err_e={err_e:.3e} err_q={err_q:.3e}")
+    if precision == "bf16" and fp16 is not None:
+        fe, fq = fp16()
+        floor = BF16_OVER_FP16 * max(fe, fq, 1e-7)
+        assert max(err_e, err_q) <= floor, (precision, err_e, err_q, "fp16", fe, fq)
+        pytest.xfail(f"bf16 storage misses the {tol:g} gate: err_e={err_e:.3e} "
+                     f"err_q={err_q:.3e}, within {BF16_OVER_FP16:g} x the fp16 error of the "
+                     f"same case ({max(fe, fq):.3e})")
     raise AssertionError((precision, err_e, err_q, tol))

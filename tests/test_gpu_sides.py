@@ -81,7 +81,14 @@ def test_sides_parity(case, kernel, precision):
         g.step(steps - g.step_count)
         o.step(steps - o.step_count)
         err_e, err_q = _compare(g, o, precision)
-        check_gate(precision, err_e, err_q)
+
+        def fp16_errors(steps=steps):
+            f, fo = _pair(case, "fp16", kernel=kernel)
+            f.step(steps)
+            fo.step(steps)
+            return _compare(f, fo, "fp16")
+
+        check_gate(precision, err_e, err_q, fp16=fp16_errors)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])

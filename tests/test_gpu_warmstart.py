@@ -5,8 +5,10 @@ import math
 import numpy as np
 import pytest
 
+import oracle
 import paper_2010_01847_gb300 as plbm
 from oracle import mlp as omlp
+from oracle import update_matrix as um
 
 pytestmark = pytest.mark.gpu
 
@@ -114,24 +116,127 @@ def test_training_reduces_loss():
     assert np.isfinite(net.params()).all()
 
 
-def test_warm_start_reaches_same_state_in_fewer_steps():
+def test_device_training_loop_matches_step_by_step():
+    """lbm_mlp_train (one captured Adam step replayed on the device) with the
+    whole set as its minibatch and a constant learning rate takes the same
+    steps as repeated lbm_mlp_train_step calls."""
+    widths = [3, 32, 24, 40]
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1, 1, (64, 3)).astype(np.float32)
+    t = rng.normal(0, 1, (64, 40)).astype(np.float32)
+    a = plbm.Mlp(widths, max_batch=64)
+    a.init_params(seed=7)
+    b = plbm.Mlp(widths, max_batch=64)
+    b.set_params(a.params())
+    hist = a.train(x, t, steps=25, batch=64, lr=2e-3, lr_final=2e-3)
+    losses = [b.train_step(x, t, 2e-3) for _ in range(25)]
+    np.testing.assert_allclose(hist, losses, rtol=1e-5)
+    np.testing.assert_allclose(a.params(), b.params(), rtol=1e-4, atol=1e-6)
+    # minibatches drawn on the device, cosine schedule: a smooth target is
+    # learnt
+    xs = rng.uniform(-1, 1, (512, 3)).astype(np.float32)
+    grid = np.linspace(0, 1, 40)
+    ts = (np.sin(2.0 * xs[:, :1] + 3.0 * grid[None, :] * xs[:, 1:2]) *
+          (1 + 0.5 * xs[:, 2:3])).astype(np.float32)
+    c = plbm.Mlp(widths, max_batch=64)
+    c.init_params(seed=1)
+    hist = c.train(xs, ts, steps=600, batch=64, lr=3e-3, lr_final=1e-4, seed=11)
+    assert np.all(np.isfinite(hist)) and hist[-50:].mean() < hist[:10].mean() / 10
+
+
+def test_analytic_profiles_follow_eq68():
+    """lbm_analytic_profiles: Eq. 68 at Y = j/255 (written from the paper
+    in the oracle's pins as a function of the Knudsen numbers), E = 0; ops
+    add and subtract."""
+    from tests.test_oracle_pins import eq68
+    cases = [(16, 32, 0.01, 1.0), (8, 301, 0.01, 100.0), (24, 64, 0.1, 0.5), (8, 17, 1.0, 2.0)]
+    inst = []
+    for nx, ny, kn_N, kn_R in cases:
+        d = ny - 1
+        inst.append(dict(nx=nx, ny=ny, tau_N=plbm.tau_from_kn(kn_N, d),
+                         tau_R=plbm.tau_from_kn(kn_R, d), bc_x=plbm.PERIODIC_GRADIENT,
+                         bc_y=plbm.DIFFUSE_WALLS, delta_e=1e-3))
+    prof = plbm.analytic_profiles(inst)
+    p = prof.cpu().numpy()
+    Y = np.arange(256) / 255
+    for k, (_, _, kn_N, kn_R) in enumerate(cases):
+        np.testing.assert_allclose(p[k, :256], eq68(Y, kn_N, kn_R), rtol=0, atol=2e-7)
+        assert np.all(p[k, 256:] == 0.0)
+    twice = plbm.analytic_profiles(inst, prof.clone(), op=1)
+    assert torch.equal(twice, 2 * prof)
+    zero = plbm.analytic_profiles(inst, prof.clone(), op=-1)
+    assert torch.count_nonzero(zero).item() == 0
+    with pytest.raises(plbm.LBMError):
+        plbm.analytic_profiles([dict(inst[0], bc_y=plbm.PERIODIC)])
+
+
+def _oracle_steady(inst):
+    """The FP64 oracle's steady state of a channel, on its shortened copy
+    (same gradient, warmstart.TRAIN_NX columns): the fixed point of the
+    oracle's explicit one-step map T (f -> T [f; 1], oracle.update_matrix),
+    solved directly with the total energy of the cold start, e = 1 at every
+    node (the walled channel conserves it).  Returns (e, qx, qy)."""
+    s = warmstart.shortened([inst])[0]
+    nx, ny = s["nx"], s["ny"]
+    p = oracle.params(s["tau_N"], s["tau_R"])
+    T = um.step_matrix(nx, ny, p["tau"], p["tau_r"], s["bc_x"], s["bc_y"], s["delta_e"])
+    n = 8 * nx * ny
+    A = np.eye(n) - T[:n, :n]
+    b = T[:n, n].copy()
+    # one equation of the singular system (energy is conserved) replaced by
+    # the total energy
+    A[0, :] = 1.0
+    b[0] = float(nx * ny)
+    f = np.linalg.solve(A, b).reshape(ny, nx, 8)
+    assert np.abs(T[:n, :n] @ f.ravel() + T[:n, n] - f.ravel()).max() < 1e-12
+    o = oracle.Lattice(nx, ny, s["tau_N"], s["tau_R"], s["bc_x"], s["bc_y"], s["delta_e"])
+    o.set_populations(f)
+    return o.moments()
+
+
+def _steady_errors(batch, k, inst, ref):
+    """err_e, err_q of instance k's end state against the oracle's steady
+    state (element by element on the full-length channel: q does not depend
+    on x, e is the reference row profile plus the affine part with the
+    steady slope -delta_e / nx)."""
+    e, qx, qy = batch.moments(k)
+    re, rqx, rqy = ref
+    nx = inst["nx"]
+    g = re.mean(axis=1) - re.mean()                     # row profile of e
+    x = np.arange(nx) - 0.5 * (nx - 1)
+    e_ref = re.mean() + g[:, None] - inst["delta_e"] / nx * x[None, :]
+    q_ref = rqx.mean(axis=1)[:, None] * np.ones((1, nx))
+    err_e = np.abs(e - e_ref).max() / np.abs(e_ref - e_ref.mean()).max()
+    err_q = max(np.abs(qx - q_ref).max(), np.abs(qy).max()) / np.abs(q_ref).max()
+    return err_e, err_q
+
+
+def test_warm_start_reaches_the_steady_state_in_fewer_steps():
     # training data: steady states of short channels from the batched solver
     train = warmstart.channels(192, seed=21, nx=warmstart.TRAIN_NX, w_range=(16, 48))
     prof, steps, r, _ = warmstart.steady_profiles(train)
     assert np.all(r < 1e-8)
     ws = warmstart.WarmStart(seed=0, max_batch=256)
-    hist = ws.train(warmstart.features(train), prof, steps=800, batch=192, lr=2e-3)
-    assert hist[-1] < hist[0] / 50
-    # held-out channels of full length 4W
-    test = warmstart.channels(12, seed=99, w_range=(16, 48))
+    hist = ws.train(train, prof, steps=800, batch=192, lr=2e-3)
+    assert hist[-1] < hist[0] / 10
+    # held-out channels of full length 4W, from three starts
+    test = warmstart.channels(12, seed=99, w_range=(16, 32))
     cold_steps, cold_r, _, cold = warmstart.solve(test)
+    ana_steps, ana_r, _, ana = warmstart.solve(test, warmstart.analytic_profiles(test))
     warm_steps, warm_r, _, warm = warmstart.solve(test, ws.predict(test))
-    assert np.all(cold_r < 1e-8) and np.all(warm_r < 1e-8)
+    for r in (cold_r, ana_r, warm_r):
+        assert np.all(r < 1e-8)
     assert warm_steps.sum() < 0.6 * cold_steps.sum(), (warm_steps, cold_steps)
-    # both runs end at the same steady state (energy is conserved, so the
-    # warm start keeps the cold start's mean energy)
-    for k in range(len(test)):
-        ce, cq, _ = cold.moments(k)
-        we, wq, _ = warm.moments(k)
-        assert np.abs(we - ce).max() <= 1e-3 * np.abs(ce - ce.mean()).max()
-        assert np.abs(wq - cq).max() <= 1e-3 * np.abs(cq).max()
+    # every start ends at the true steady state (the FP64 oracle's), and the
+    # learned start at least as close as the others: the solves stop at
+    # r < 1e-8 over 100-step windows, which leaves the slowest mode at about
+    # r / (its decay rate per step) of the state; 1e-3 bounds that for
+    # channels of these widths (W <= 32), and FP32 storage adds ~1e-6
+    errs = {"cold": [], "analytic": [], "learned": []}
+    for k, inst in enumerate(test):
+        ref = _oracle_steady(inst)
+        for name, b in (("cold", cold), ("analytic", ana), ("learned", warm)):
+            errs[name].append(_steady_errors(b, k, inst, ref))
+    worst = {n: np.max(v) for n, v in errs.items()}
+    assert all(w <= 1e-3 for w in worst.values()), worst
+    assert worst["learned"] <= 2.0 * max(worst["cold"], worst["analytic"]) + 1e-6, worst
