@@ -10,6 +10,7 @@
 // layer inputs feed the products.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -20,8 +21,8 @@
 namespace plbm {
 namespace {
 
-constexpr int TM = 64, TN = 64, TK = 32;    // block tile
-constexpr int GEMM_THREADS = 128;          // 4 warps, 32 x 32 each
+constexpr int TK = 32;                     // k depth of a block tile
+constexpr int GEMM_THREADS = 128;          // 4 warps
 
 __device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
@@ -53,37 +54,101 @@ enum { EPI_NONE = 0, EPI_GELU = 1, EPI_GELU_BWD = 2 };
 // out = the FP32 result after the epilogue, outb = the same in BF16.
 // Epilogues: GELU (forward), GELU backward (the result times GELU'(aux[m, n]),
 // aux the pre-activation of the layer below: dZ = dX (.) GELU'(Z)).
+// Block tile BM x BN (64 or 32 each), four warps of (BM / 2) x (BN / 2).
+template <int BM, int BN>
 __global__ void __launch_bounds__(GEMM_THREADS)
 gemm_bf16(const __nv_bfloat16 *__restrict__ A, long long am, long long ak,
           const __nv_bfloat16 *__restrict__ B, long long bk, long long bn,
           const float *__restrict__ bias, int M, int N, int K, int epi,
           const float *__restrict__ aux, float *__restrict__ pre, float *__restrict__ out,
           __nv_bfloat16 *__restrict__ outb) {
-    __shared__ __nv_bfloat16 As[TM][TK + 8];
-    __shared__ __nv_bfloat16 Bs[TN][TK + 8];     // stored [n][k]
-    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    __shared__ __align__(16) __nv_bfloat16 As[BM][TK + 8];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][TK + 8];     // stored [n][k]
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    constexpr int MI = BM / 32, NJ = BN / 16;     // m16 x n8 tiles per warp
+    const int wm = (warp >> 1) * (BM / 2), wn = (warp & 1) * (BN / 2);
     const int g = lane >> 2, tg = lane & 3;
-    float acc[2][4][4] = {};
+    float acc[MI][NJ][4] = {};
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    // The tiles are filled along the operand's contiguous index with 16-byte
+    // loads (8 values) where the rows are 16-byte aligned, element by element
+    // otherwise (the first layer's 3 inputs) and at the matrix edges.
+    const bool a_k_vec = ak == 1 && am % 8 == 0 && ((uintptr_t)A & 15) == 0;
+    const bool a_m_vec = am == 1 && ak % 8 == 0 && ((uintptr_t)A & 15) == 0;
+    const bool b_k_vec = bk == 1 && bn % 8 == 0 && ((uintptr_t)B & 15) == 0;
+    const bool b_n_vec = bn == 1 && bk % 8 == 0 && ((uintptr_t)B & 15) == 0;
     for (int k0 = 0; k0 < K; k0 += TK) {
-        for (int idx = threadIdx.x; idx < TM * TK; idx += GEMM_THREADS) {
-            const int r = idx / TK, c = idx % TK;
-            const int m = m0 + r, k = k0 + c;
-            As[r][c] = (m < M && k < K) ? A[(long long)m * am + (long long)k * ak] : zero;
+        if (a_k_vec) {
+            for (int idx = threadIdx.x; idx < BM * TK / 8; idx += GEMM_THREADS) {
+                const int r = idx / (TK / 8), c = (idx % (TK / 8)) * 8;
+                const int m = m0 + r, k = k0 + c;
+                if (m < M && k + 8 <= K) {
+                    *reinterpret_cast<uint4 *>(&As[r][c]) =
+                        *reinterpret_cast<const uint4 *>(A + (long long)m * am + k);
+                } else {
+                    for (int j = 0; j < 8; ++j)
+                        As[r][c + j] = (m < M && k + j < K) ? A[(long long)m * am + k + j] : zero;
+                }
+            }
+        } else if (a_m_vec) {
+            for (int idx = threadIdx.x; idx < BM * TK / 8; idx += GEMM_THREADS) {
+                const int c = idx / (BM / 8), r = (idx % (BM / 8)) * 8;
+                const int m = m0 + r, k = k0 + c;
+                if (k < K && m + 8 <= M) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(A + m + (long long)k * ak);
+                    const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&v);
+                    for (int j = 0; j < 8; ++j) As[r + j][c] = h[j];
+                } else {
+                    for (int j = 0; j < 8; ++j)
+                        As[r + j][c] = (k < K && m + j < M) ? A[m + j + (long long)k * ak] : zero;
+                }
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < BM * TK; idx += GEMM_THREADS) {
+                const int r = idx / TK, c = idx % TK;
+                const int m = m0 + r, k = k0 + c;
+                As[r][c] = (m < M && k < K) ? A[(long long)m * am + (long long)k * ak] : zero;
+            }
         }
-        for (int idx = threadIdx.x; idx < TN * TK; idx += GEMM_THREADS) {
-            const int r = idx / TK, c = idx % TK;
-            const int n = n0 + r, k = k0 + c;
-            Bs[r][c] = (n < N && k < K) ? B[(long long)k * bk + (long long)n * bn] : zero;
+        if (b_k_vec) {
+            for (int idx = threadIdx.x; idx < BN * TK / 8; idx += GEMM_THREADS) {
+                const int r = idx / (TK / 8), c = (idx % (TK / 8)) * 8;
+                const int n = n0 + r, k = k0 + c;
+                if (n < N && k + 8 <= K) {
+                    *reinterpret_cast<uint4 *>(&Bs[r][c]) =
+                        *reinterpret_cast<const uint4 *>(B + k + (long long)n * bn);
+                } else {
+                    for (int j = 0; j < 8; ++j)
+                        Bs[r][c + j] = (n < N && k + j < K) ? B[k + j + (long long)n * bn] : zero;
+                }
+            }
+        } else if (b_n_vec) {
+            for (int idx = threadIdx.x; idx < BN * TK / 8; idx += GEMM_THREADS) {
+                const int c = idx / (BN / 8), r = (idx % (BN / 8)) * 8;
+                const int n = n0 + r, k = k0 + c;
+                if (k < K && n + 8 <= N) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(B + (long long)k * bk + n);
+                    const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&v);
+                    for (int j = 0; j < 8; ++j) Bs[r + j][c] = h[j];
+                } else {
+                    for (int j = 0; j < 8; ++j)
+                        Bs[r + j][c] = (k < K && n + j < N) ? B[(long long)k * bk + n + j] : zero;
+                }
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < BN * TK; idx += GEMM_THREADS) {
+                const int r = idx / TK, c = idx % TK;
+                const int n = n0 + r, k = k0 + c;
+                Bs[r][c] = (n < N && k < K) ? B[(long long)k * bk + (long long)n * bn] : zero;
+            }
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < TK; kk += 16) {
-            unsigned a[2][4], b[4][2];
+            unsigned a[MI][4], b[NJ][2];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
+            for (int i = 0; i < MI; ++i) {
                 const int r = wm + 16 * i + g;
                 a[i][0] = pack_bf16(As[r][kk + 2 * tg], As[r][kk + 2 * tg + 1]);
                 a[i][1] = pack_bf16(As[r + 8][kk + 2 * tg], As[r + 8][kk + 2 * tg + 1]);
@@ -91,22 +156,22 @@ gemm_bf16(const __nv_bfloat16 *__restrict__ A, long long am, long long ak,
                 a[i][3] = pack_bf16(As[r + 8][kk + 2 * tg + 8], As[r + 8][kk + 2 * tg + 9]);
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < NJ; ++j) {
                 const int c = wn + 8 * j + g;
                 b[j][0] = pack_bf16(Bs[c][kk + 2 * tg], Bs[c][kk + 2 * tg + 1]);
                 b[j][1] = pack_bf16(Bs[c][kk + 2 * tg + 8], Bs[c][kk + 2 * tg + 9]);
             }
 #pragma unroll
-            for (int i = 0; i < 2; ++i)
+            for (int i = 0; i < MI; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
+                for (int j = 0; j < NJ; ++j) mma_bf16(acc[i][j], a[i], b[j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < MI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < NJ; ++j)
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const int m = m0 + wm + 16 * i + g + (h >= 2 ? 8 : 0);
@@ -170,22 +235,31 @@ bias_grad(const float *__restrict__ dz, int B, int N, float *__restrict__ db) {
     }
 }
 
+// One Adam update of parameter i (refreshing its BF16 copy if it is a weight).
+__device__ __forceinline__ void adam_update(long long i, float *__restrict__ p,
+                                            const float *__restrict__ g, float *__restrict__ m,
+                                            float *__restrict__ v, float lr, float b1, float b2,
+                                            float eps, float c1, float c2,
+                                            const long long *__restrict__ wmap,
+                                            __nv_bfloat16 *__restrict__ pb) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float w = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = w;
+    if (wmap[i] >= 0) pb[wmap[i]] = __float2bfloat16_rn(w);
+}
+
 // Adam on the flat FP32 parameters, refreshing the BF16 copy of every weight.
 __global__ void adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                      float *__restrict__ v, long long n, float lr, float b1, float b2, float eps,
                      float c1, float c2, const long long *__restrict__ wmap,
                      __nv_bfloat16 *__restrict__ pb) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        const float w = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        p[i] = w;
-        if (wmap[i] >= 0) pb[wmap[i]] = __float2bfloat16_rn(w);
-    }
+         i += (long long)gridDim.x * blockDim.x)
+        adam_update(i, p, g, m, v, lr, b1, b2, eps, c1, c2, wmap, pb);
 }
 
 // Per-step scalars of the device training loop (train_setup writes them).
@@ -253,16 +327,8 @@ __global__ void adam_dev(float *__restrict__ p, const float *__restrict__ g,
                          const long long *__restrict__ wmap, __nv_bfloat16 *__restrict__ pb) {
     const float lr = st->lr, c1 = st->c1, c2 = st->c2;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        const float w = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        p[i] = w;
-        if (wmap[i] >= 0) pb[wmap[i]] = __float2bfloat16_rn(w);
-    }
+         i += (long long)gridDim.x * blockDim.x)
+        adam_update(i, p, g, m, v, lr, b1, b2, eps, c1, c2, wmap, pb);
 }
 
 unsigned grid1(long long n) {
@@ -325,9 +391,18 @@ cudaError_t gemm(cudaStream_t s, const __nv_bfloat16 *A, long long am, long long
                  const __nv_bfloat16 *B, long long bk, long long bn, const float *bias, int M,
                  int N, int K, int epi, const float *aux, float *pre, float *out,
                  __nv_bfloat16 *outb) {
-    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-    gemm_bf16<<<grid, GEMM_THREADS, 0, s>>>(A, am, ak, B, bk, bn, bias, M, N, K, epi, aux, pre,
-                                            out, outb);
+    // 64 x 64 tiles when they give at least two blocks per SM, else 32 x 32
+    // (the network's products are small: a few hundred rows and columns)
+    const long long big = (long long)((N + 63) / 64) * ((M + 63) / 64);
+    if (big >= 2 * 152) {
+        dim3 grid((N + 63) / 64, (M + 63) / 64);
+        gemm_bf16<64, 64><<<grid, GEMM_THREADS, 0, s>>>(A, am, ak, B, bk, bn, bias, M, N, K,
+                                                        epi, aux, pre, out, outb);
+    } else {
+        dim3 grid((N + 31) / 32, (M + 31) / 32);
+        gemm_bf16<32, 32><<<grid, GEMM_THREADS, 0, s>>>(A, am, ak, B, bk, bn, bias, M, N, K,
+                                                        epi, aux, pre, out, outb);
+    }
     return cudaGetLastError();
 }
 
