@@ -71,10 +71,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="heat_mode",
-                    choices=["heat_mode", "batch", "warmstart", "d3q14", "small"],
+                    choices=["heat_mode", "batch", "warmstart", "train", "d3q14", "small"],
                     help="heat_mode: 8192^2 throughput (default); batch: 512 channels "
                          "solved to steady state; warmstart: learned warm start vs cold "
-                         "start on 512 held-out channels; d3q14: 3-D D3Q14 throughput "
+                         "start on 512 held-out channels; train: the warm-start network's "
+                         "training speed alone; d3q14: 3-D D3Q14 throughput "
                          "on a periodic nz x ny x nx lattice (--n3 cells per side); small: "
                          "the 128x32 Poiseuille channel (FP64, FP32) and the 4096x4 "
                          "second-sound pulse (FP32), time per step and error vs the oracle")
@@ -92,7 +93,9 @@ def parse():
                          "reference (warmstart workload)")
     ap.add_argument("--no-steady", action="store_true",
                     help="default workload: skip the time-to-steady-state leg")
-    ap.add_argument("--sequential-sample", type=int, default=16)
+    ap.add_argument("--sequential-sample", type=int, default=0,
+                    help="batch workload: channels of the one-at-a-time baseline "
+                         "(0 = all of them)")
     return ap.parse_args()
 
 
@@ -253,11 +256,11 @@ def measured_peak():
 
 # sources that define each stream-collide kernel
 KERNEL_SOURCES = {
-    "step_vector": ["lbm_device.cuh", "pairs16.cuh", "vector_pull.cuh", "stream_collide.cu"],
+    "step_vector": ["lbm_device.cuh", "vector_pull.cuh", "stream_collide.cu"],
     "step_pipe16": ["lbm_device.cuh", "refs16.cuh", "pairs16.cuh", "vector_pull.cuh",
                     "pipe16.cu"],
-    "step_staged": ["lbm_device.cuh", "pairs16.cuh", "staged.cu"],
-    "step_scalar": ["lbm_device.cuh", "pairs16.cuh", "stream_collide.cu"],
+    "step_staged": ["lbm_device.cuh", "mbarrier.cuh", "staged.cu"],
+    "step_scalar": ["lbm_device.cuh", "refs16.cuh", "stream_collide.cu"],
 }
 
 
@@ -663,8 +666,9 @@ def batch_instances(n, seed=inputs.SEED):
 
 def run_batch(args):
     """Time to steady state (r < tol on two consecutive checks every
-    --check-every steps) of the batched channels from a cold start (e = 1, q = 0), with
-    the plain single-lattice solver on a sample of them as the baseline."""
+    --check-every steps) of the batched channels from a cold start (e = 1,
+    q = 0), with the plain single-lattice solver run on every channel, one
+    after the other, as the baseline."""
     import torch
     import paper_2010_01847_gb300 as plbm
     torch.cuda.set_device(0)
@@ -679,10 +683,16 @@ def run_batch(args):
     steps, r = b.solve(args.tol, args.check_every, args.max_steps)
     t_batch = time.perf_counter() - t0
     updates = float((steps * sites).sum())
-    # plain solver, one lattice at a time, on a seeded sample
-    rng = np.random.default_rng(5)
-    sample = sorted(rng.choice(len(inst), size=min(args.sequential_sample, len(inst)),
-                               replace=False).tolist())
+    # the plain single-lattice solver, one channel at a time (the fastest
+    # kernel each: cluster-resident up to 16384 nodes, else the vector
+    # kernel in 64-step graphs, the residual fused every check window): all
+    # channels, or a seeded sample with --sequential-sample n > 0
+    if args.sequential_sample > 0:
+        rng = np.random.default_rng(5)
+        sample = sorted(rng.choice(len(inst), size=min(args.sequential_sample, len(inst)),
+                                   replace=False).tolist())
+    else:
+        sample = list(range(len(inst)))
     t_seq = 0.0
     seq_updates = 0.0
     for k in sample:
@@ -705,7 +715,8 @@ def run_batch(args):
         lat.close()
     cpu = None
     if not args.no_cpu:
-        g_cpu, cores, desc = oracle_rate([inst[k] for k in sample[:4]], args.cpu_seconds)
+        g_cpu, cores, desc = oracle_rate([inst[k] for k in sample[::max(1, len(sample) // 4)][:4]],
+                                         args.cpu_seconds)
         cpu = {"value": g_cpu, "unit": "GLUPS", "cores": cores, "kind": "oracle",
                "sample": desc, "estimated_seconds_all": updates / (g_cpu * 1e9)}
     line = {
@@ -720,10 +731,14 @@ def run_batch(args):
         "steps": {"min": int(steps.min()), "median": float(np.median(steps)),
                   "max": int(steps.max()), "all_converged": bool(np.all(r < args.tol))},
         "site_updates": updates, "glups": updates / t_batch / 1e9,
-        "plain_sequential_sample": {
-            "instances": len(sample), "seconds": t_seq, "site_updates": seq_updates,
+        "plain_sequential": {
+            "instances": len(sample), "measured_all": len(sample) == len(inst),
+            "seconds": t_seq, "site_updates": seq_updates,
             "glups": seq_updates / t_seq / 1e9,
-            "estimated_seconds_all": t_seq * updates / max(seq_updates, 1.0)},
+            "seconds_all": t_seq if len(sample) == len(inst)
+            else t_seq * updates / max(seq_updates, 1.0)},
+        "batched_over_sequential": (t_seq if len(sample) == len(inst)
+                                    else t_seq * updates / max(seq_updates, 1.0)) / t_batch,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -808,6 +823,37 @@ def steady_state_study(n_train, train_steps, n_test, n_ref, tol, check_every, ma
     return out
 
 
+def run_train(args):
+    """Training speed of the warm-start network alone: --train-steps Adam
+    steps (the device training loop, lbm_mlp_train) on minibatches of 512
+    from --train-instances synthetic samples (inputs uniform in [-1, 1],
+    targets N(0, 0.1^2); the time does not depend on the values)."""
+    import torch
+    import paper_2010_01847_gb300 as plbm
+    from paper_2010_01847_gb300 import warmstart
+    torch.cuda.set_device(0)
+    n = args.train_instances
+    rng = np.random.default_rng(inputs.SEED)
+    x = torch.from_numpy(rng.uniform(-1, 1, (n, warmstart.WIDTHS[0])).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(0, 0.1, (n, warmstart.WIDTHS[-1])).astype(np.float32)).cuda()
+    net = plbm.Mlp(list(warmstart.WIDTHS), max_batch=max(512, n))
+    net.init_params(0)
+    net.train(x, t, 10, 512, 1e-3, 1e-5)          # capture, first launches (untimed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = net.train(x, t, args.train_steps, 512, 1e-3, 1e-5)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    line = {"metric": "warm-start network training time", "value": dt, "unit": "s",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "bf16 products / f32",
+            "data": "synthetic",
+            "config": {"workload": f"train_{args.train_steps}_steps", "samples": n,
+                       "batch": 512, "network": list(warmstart.WIDTHS)},
+            "ms_per_step": dt / args.train_steps * 1e3,
+            "loss_first": float(hist[0]), "loss_last": float(hist[-1])}
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args):
     """Learned warm start on the full held-out set: steady states of seeded
     training channels from the batched solver, the network trained on the
@@ -841,6 +887,8 @@ def main():
         run_batch(args)
     elif args.workload == "warmstart":
         run_warmstart(args)
+    elif args.workload == "train":
+        run_train(args)
     elif args.workload == "d3q14":
         run_d3q14(args)
     elif args.workload == "small":
