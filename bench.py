@@ -11,9 +11,11 @@ into that step's launch.  The population buffers (2 x 2.1 GB) exceed
 the 129 MB L2, so no flush is needed between steps.
 
 Metric: GLUPS (10^9 lattice-site updates per second, whole job).  Also
-reported: the roofline of the stream-collide kernel (algorithmic bytes: one
-state buffer read and one written per site update, over its CUDA-event
-time), an end-to-end figure through the public API with host buffers, the
+reported: the roofline of the dominant stream-collide kernel (algorithmic
+bytes: one state buffer read and one written per launch, which is one site
+update for the single-step kernels and several for the multi-step kernel,
+over its mean launch time from the library's CUDA events on the lattice's
+stream), an end-to-end figure through the public API with host buffers, the
 FP64 oracle on the host cores as a CPU baseline, and (``steady_state``) the
 metric's second half: time to steady state (r < 1e-8) of 64 held-out
 channels from the cold, the analytic (Eq. 68) and the learned start, with
@@ -63,6 +65,10 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32", choices=list(STORAGE_BYTES))
     ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--wave-steps", type=int, default=0,
+                    help="multi-step kernel: steps per launch (0 = autotuned or default)")
+    ap.add_argument("--wave-rows", type=int, default=0,
+                    help="multi-step kernel: rows per segment (0 = autotuned or default)")
     ap.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
                     help="rounding of 16-bit storage")
     ap.add_argument("--nx", type=int, default=inputs.THROUGHPUT_8192.nx)
@@ -261,6 +267,7 @@ KERNEL_SOURCES = {
                     "pipe16.cu"],
     "step_staged": ["lbm_device.cuh", "mbarrier.cuh", "staged.cu"],
     "step_scalar": ["lbm_device.cuh", "refs16.cuh", "stream_collide.cu"],
+    "step_wave": ["lbm_device.cuh", "wave.cu"],
 }
 
 
@@ -368,8 +375,11 @@ def run_native(args):
     lat.init(e_dev, z_dev, z_dev)
     tuned = None
     if args.kernel == "auto":
-        # set-up, untimed: pick the fastest kernel / staged shape on this GPU
+        # set-up, untimed: pick the fastest kernel / shape on this GPU
         tuned = lat.autotune(20)
+    if args.wave_steps or args.wave_rows:
+        wc = lat.wave_config
+        lat.set_wave_config(args.wave_steps or wc["steps"], args.wave_rows or wc["rows"])
     stream = torch.cuda.current_stream(dev)
 
     # residual window: every RESIDUAL_EVERY-th step, or once per run when
@@ -377,42 +387,35 @@ def run_native(args):
     # residual's cost (at a higher weight than a long one)
     window = max(1, min(RESIDUAL_EVERY, args.steps))
 
-    def chunked(nsteps, events=None):
-        """Advance nsteps; the last step of every window also reduces the
-        residual inside its stream-collide launch (lbm_step_residual).
-        Events bracket each run of plain stream-collide launches."""
+    def chunked(nsteps):
+        """Advance nsteps in windows: each whole window is one
+        lbm_step_residual call, whose last step also reduces the residual
+        inside its stream-collide launch; a shorter tail is plain steps."""
         done = 0
-        launches = 0
         while done < nsteps:
             k = min(window, nsteps - done)
-            plain = k - 1 if k == window else k
-            if events is not None:
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-            lat.step(plain)
-            if events is not None:
-                b.record(stream)
-                events.append((a, b, plain))
-            launches += plain
-            if plain < k:
-                lat.step_residual(1)   # fused step + fixed-order total
-                launches += 1
+            if k == window:
+                lat.step_residual(k)
+            else:
+                lat.step(k)
             done += k
-        return launches
 
     chunked(max(args.warmup, 3))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    events = []
     sampler = ClockSampler(dev.index)
     launches0 = lat.kernel_launches
+    # the library brackets every stream-collide launch with CUDA events on
+    # the lattice's stream (no graphs meanwhile: at these sizes a launch is
+    # far longer than its launch latency)
+    lat.set_launch_timing(True)
     with sampler:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        chunked(args.steps, events)
+        chunked(args.steps)
         t1.record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -420,26 +423,43 @@ def run_native(args):
     torch.cuda.synchronize()
     elapsed = t0.elapsed_time(t1) / 1e3
     launches = lat.kernel_launches - launches0        # counted by the library
-    kern_s = sum(a.elapsed_time(b) for a, b, _ in events) / 1e3
-    kern_steps = sum(k for _, _, k in events)
+    timed = {which: lat.launch_time(which)
+             for which in (plbm.TIMED_WAVE, plbm.TIMED_SINGLE, plbm.TIMED_RESIDUAL)}
+    lat.set_launch_timing(False)
     elapsed = max_over_ranks(elapsed, dist, dev)
     sites = nx * ny
     value = job_value(world, sites, args.steps, elapsed)
 
-    # roofline of the stream-collide kernel: one state buffer read and one
-    # written per site (16-bit storage includes the tiles' references)
+    # roofline of the dominant stream-collide kernel (the kind of launch
+    # with the most time): one state buffer read and one written per launch
+    # (16-bit storage includes the tiles' references), i.e. per site update
+    # for single steps and per `steps / launches` updates for the
+    # multi-step kernel
     bps = lat.bytes_per_site_update
-    avg_launch = kern_s / kern_steps
+    dom = max(timed, key=lambda w: timed[w][0])
+    kern_ms, kern_launches, kern_steps = timed[dom]
+    avg_launch = kern_ms / 1e3 / kern_launches
     achieved = bps * sites / avg_launch / 1e9
     peak, peak_kind = measured_peak()
-    kname = "step_" + lat.kernel
-    if lat.kernel == "vector" and STORAGE_BYTES[args.precision] == 2:
-        kname = "step_pipe16"               # plain 16-bit steps: the pipelined node-pair kernel
+    if dom == plbm.TIMED_WAVE:
+        kname = "step_wave"
+    elif dom == plbm.TIMED_RESIDUAL:
+        kname = "step_vector_residual"
+    else:
+        kname = "step_" + ("vector" if lat.kernel == "wave" else lat.kernel)
+        if kname == "step_vector" and STORAGE_BYTES[args.precision] == 2:
+            kname = "step_pipe16"           # plain 16-bit steps: the pipelined node-pair kernel
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": ncu_traffic(kname, args.precision, nx, ny),
             "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else 'profiling-recipe fallback 6.8 TB/s'})",
-            "kernel": kname, "bytes_per_site_update": bps,
-            "avg_launch_us": avg_launch * 1e6}
+            "kernel": kname, "bytes_per_launch_site": bps,
+            "steps_per_launch": kern_steps / kern_launches,
+            "bytes_per_site_update": bps * kern_launches / kern_steps,
+            "avg_launch_us": avg_launch * 1e6,
+            "launch_mix": {n: {"ms": v[0], "launches": v[1], "steps": v[2]}
+                           for n, v in (("multi_step", timed[plbm.TIMED_WAVE]),
+                                        ("single", timed[plbm.TIMED_SINGLE]),
+                                        ("residual", timed[plbm.TIMED_RESIDUAL]))}}
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -476,6 +496,7 @@ def run_native(args):
     # second half), on a bounded held-out set: one GPU, rank 0 alone
     kernel_name = lat.kernel
     staged_shape = lat.staged_config if kernel_name == "staged" else None
+    wave_shape = lat.wave_config if kernel_name == "wave" else None
     steady = None
     if rank == 0 and world == 1 and not args.no_steady:
         lat.close()
@@ -499,6 +520,7 @@ def run_native(args):
                                     if STORAGE_BYTES[args.precision] == 2 else "")),
                        "kernel": kernel_name,
                        "staged_shape": staged_shape,
+                       "wave_shape": wave_shape,
                        "autotuned": tuned is not None,
                        "residual_every": window,
                        "l2": "inputs larger than L2 (2 x population buffers >> 129 MB); "

@@ -133,7 +133,7 @@ typedef enum {
                              /* segments into a shared-memory ring; needs nx  */
                              /* a multiple of the tile width (4096/size with  */
                              /* the default shape)                            */
-    LBM_KERNEL_RESIDENT = 4  /* LBM_FP32 lattices small enough that both      */
+    LBM_KERNEL_RESIDENT = 4, /* LBM_FP32 lattices small enough that both      */
                              /* population buffers fit in the shared memory   */
                              /* of one thread-block cluster (up to 16 CTAs,   */
                              /* ~3.6 MB: 201 x 201 fits): lbm_step(n) is one  */
@@ -142,6 +142,18 @@ typedef enum {
                              /* for bit.  lbm_set_kernel returns              */
                              /* LBM_EUNSUPPORTED when the lattice does not    */
                              /* fit or no cluster can be resident             */
+    LBM_KERNEL_WAVE = 5      /* several steps per launch (temporal blocking): */
+                             /* each warp advances a 64-column strip of a     */
+                             /* segment of rows K levels in registers         */
+                             /* (lbm_set_wave_config), reading and writing    */
+                             /* the planes once per K steps; same results bit */
+                             /* for bit.  LBM_FP32 storage, nx even, x        */
+                             /* periodic (with or without the gradient), y    */
+                             /* periodic or walled; else LBM_EUNSUPPORTED.    */
+                             /* lbm_step(n) ends with one single step (vector */
+                             /* kernel, else scalar), which the read-outs     */
+                             /* need; lbm_step_residual(n) runs n - 1 steps   */
+                             /* in multi-step launches and its residual step  */
 } lbm_kernel;
 
 typedef struct {
@@ -312,7 +324,9 @@ lbm_status lbm_get_staged_config(const lbm_ctx *ctx, int *stages, int *ctas_per_
 
 /* Autotuner: times every stream-collide kernel and staged shape that can
  * run this lattice (vector or scalar; staged with 2 or 3 stages and 8 or 4
- * consumer warps), trial_steps steps each (0 = 20) after 2 warm-up steps,
+ * consumer warps; cluster-resident; the multi-step kernel with 4, 5 or 6
+ * steps per launch and segments of 64 or 128 rows, on lattices of at least
+ * 128 x 64 nodes), trial_steps steps each (0 = 20) after 2 warm-up steps,
  * on the context's stream, and keeps the fastest for later lbm_step calls.
  * The timings run on the context's own buffers; when the context holds a
  * state (after lbm_init) both buffers are first copied to a temporary
@@ -323,8 +337,34 @@ lbm_status lbm_get_staged_config(const lbm_ctx *ctx, int *stages, int *ctas_per_
 lbm_status lbm_autotune(lbm_ctx *ctx, int trial_steps, int *kernel, double *us_per_step);
 
 /* Steps per captured CUDA graph chunk (even, >= 2), or 0 to launch every
- * step directly.  Default 64. */
+ * step directly.  Default 64.  With LBM_KERNEL_WAVE a graph holds an even
+ * number of multi-step launches of about this many steps. */
 lbm_status lbm_set_graph_chunk(lbm_ctx *ctx, int steps);
+
+/* Shape of the multi-step kernel (LBM_KERNEL_WAVE): `steps` time steps per
+ * launch (2..8) and strips of `rows` rows (>= 1; clipped to ny).  A launch
+ * reads and writes the planes once: 64 B per node per `steps` steps, plus
+ * the 2 x steps rows of overlap each segment reads.  Each warp keeps about
+ * 27 registers per step level (steps = 4: 168 per thread).  Defaults 4 and
+ * 128; lbm_autotune sets both.  EINVAL out of range. */
+lbm_status lbm_set_wave_config(lbm_ctx *ctx, int steps, int rows);
+lbm_status lbm_get_wave_config(const lbm_ctx *ctx, int *steps, int *rows);
+
+/* Launch timing (no counterpart in the paper).  While on, lbm_step and
+ * lbm_step_residual bracket every stream-collide launch with a pair of CUDA
+ * events on the context's stream and launch without graphs.  Turning it on
+ * or off synchronises the stream and clears the totals.  lbm_launch_time
+ * synchronises and returns, for one kind of launch, the summed event time
+ * in milliseconds, the number of launches and the time steps they advanced
+ * since timing was turned on (outputs may be NULL): */
+typedef enum {
+    LBM_TIMED_WAVE = 0,      /* multi-step launches (LBM_KERNEL_WAVE)          */
+    LBM_TIMED_SINGLE = 1,    /* single-step launches                           */
+    LBM_TIMED_RESIDUAL = 2   /* the step of lbm_step_residual (with its sums)  */
+} lbm_timed;
+lbm_status lbm_set_launch_timing(lbm_ctx *ctx, int on);
+lbm_status lbm_launch_time(lbm_ctx *ctx, int which, double *ms, long long *launches,
+                           long long *steps);
 
 /* Number of stream-collide kernel launches queued since lbm_init. */
 long long lbm_kernel_launches(const lbm_ctx *ctx);

@@ -25,14 +25,15 @@ PERIODIC, PERIODIC_GRADIENT, DIFFUSE_WALLS, SIDES = 0, 1, 2, 3
 LEFT, RIGHT, BOTTOM, TOP = 0, 1, 2, 3                 # sides (lbm_side)
 DIFFUSE, ISOTHERMAL, HEAT_FLUX = 0, 1, 2              # side treatments (lbm_side_kind)
 FP32, FP16_DEV, BF16_DEV, FP64 = 0, 1, 2, 3
-KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_STAGED, KERNEL_RESIDENT = 0, 1, 2, 3, 4
+KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_STAGED, KERNEL_RESIDENT, KERNEL_WAVE = range(6)
+TIMED_WAVE, TIMED_SINGLE, TIMED_RESIDUAL = 0, 1, 2     # lbm_timed
 
 D1Q2, D3Q14 = 1, 3                                     # lbm_lattice
 PRECISIONS = {"fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV, "fp64": FP64}
 ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1
 ROUNDINGS = {"nearest": ROUND_NEAREST, "stochastic": ROUND_STOCHASTIC}
 KERNELS = {"auto": KERNEL_AUTO, "scalar": KERNEL_SCALAR, "vector": KERNEL_VECTOR,
-           "staged": KERNEL_STAGED, "resident": KERNEL_RESIDENT}
+           "staged": KERNEL_STAGED, "resident": KERNEL_RESIDENT, "wave": KERNEL_WAVE}
 _ELEM = {FP32: 4, FP16_DEV: 2, BF16_DEV: 2, FP64: 8}
 
 # Every symbol include/phonon_lbm.h declares.
@@ -44,7 +45,8 @@ EXPORTS = [
     "lbm_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_step_count",
     "lbm_set_kernel", "lbm_get_kernel", "lbm_set_side", "lbm_get_side",
     "lbm_set_staged_config", "lbm_get_staged_config", "lbm_set_rounding",
-    "lbm_set_graph_chunk", "lbm_autotune",
+    "lbm_set_graph_chunk", "lbm_autotune", "lbm_set_wave_config", "lbm_get_wave_config",
+    "lbm_set_launch_timing", "lbm_launch_time",
     "lbm_kernel_launches", "lbm_storage_scale", "lbm_last_error",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_init", "lbm_batch_step",
     "lbm_batch_residuals", "lbm_batch_solve", "lbm_batch_moments", "lbm_batch_set_schedule",
@@ -124,6 +126,12 @@ def load_library(path: str = LIB_PATH):
         "lbm_get_side": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
         "lbm_set_graph_chunk": (st, [vp, ctypes.c_int]),
         "lbm_autotune": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
+        "lbm_set_wave_config": (st, [vp, ctypes.c_int, ctypes.c_int]),
+        "lbm_get_wave_config": (st, [vp, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]),
+        "lbm_set_launch_timing": (st, [vp, ctypes.c_int]),
+        "lbm_launch_time": (st, [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ctypes.c_longlong)]),
         "lbm_set_rounding": (st, [vp, ctypes.c_int]),
         "lbm_set_staged_config": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int]),
@@ -476,6 +484,30 @@ class Lattice:
 
     def set_graph_chunk(self, steps: int):
         self._check(self._lib.lbm_set_graph_chunk(self._ctx, int(steps)))
+
+    def set_wave_config(self, steps: int, rows: int):
+        """Steps per launch and rows per segment of the multi-step kernel
+        (lbm_set_wave_config)."""
+        self._check(self._lib.lbm_set_wave_config(self._ctx, int(steps), int(rows)))
+
+    @property
+    def wave_config(self):
+        v = [ctypes.c_int() for _ in range(2)]
+        self._check(self._lib.lbm_get_wave_config(self._ctx, *[ctypes.byref(x) for x in v]))
+        return {"steps": v[0].value, "rows": v[1].value}
+
+    def set_launch_timing(self, on: bool):
+        """Event pairs around every stream-collide launch (lbm_set_launch_timing)."""
+        self._check(self._lib.lbm_set_launch_timing(self._ctx, int(bool(on))))
+
+    def launch_time(self, which: int):
+        """(milliseconds, launches, steps) of one kind of launch since timing
+        was turned on (lbm_launch_time; TIMED_WAVE, TIMED_SINGLE or
+        TIMED_RESIDUAL)."""
+        ms, n, k = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(self._lib.lbm_launch_time(self._ctx, int(which), ctypes.byref(ms),
+                                              ctypes.byref(n), ctypes.byref(k)))
+        return ms.value, n.value, k.value
 
     @property
     def bytes_per_site_update(self) -> float:

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <type_traits>
 #include <string>
+#include <vector>
 
 #include "../../include/phonon_lbm.h"
 #include "lbm_kernels.h"
@@ -40,7 +41,15 @@ struct lbm_ctx {
     int stages_req = 0, ctas_req = 0, cw_req = 0, hint_req = 0;
     ResidentPlan rplan;         // launch shape of the cluster-resident kernel
     int cluster_req = 0;
+    int wave_steps = 4;         // multi-step kernel: steps per launch
+    int wave_rows = 128;        // and rows per strip segment
     int graph_chunk = 64;
+    // launch timing (lbm_set_launch_timing): event pairs around launches
+    bool timing = false;
+    struct Timed { cudaEvent_t a, b; int which; long steps; };
+    std::vector<Timed> timed;
+    double timed_ms[3] = {0.0, 0.0, 0.0};
+    long long timed_launches[3] = {0, 0, 0}, timed_steps[3] = {0, 0, 0};
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     void *prev = nullptr;       // residual history, 3 planes of the compute type
@@ -361,6 +370,8 @@ int resolve_kernel(lbm_ctx *c, int requested) {
     // 5.3-5.6 against 6.2 us per step)
     if (requested == KERNEL_AUTO && c->precision == PREC_FP64 && c->plane <= RESIDENT_AUTO_NODES)
         return KERNEL_SCALAR;
+    if (requested == KERNEL_WAVE)
+        return wave_supported(c->precision, c->nx, c->ny, c->bc_x, c->bc_y) ? KERNEL_WAVE : -1;
     if (has_sides(c)) {     // the per-side rules: scalar, vector and resident kernels
         if (requested == KERNEL_AUTO) return vec_ok ? KERNEL_VECTOR : KERNEL_SCALAR;
         if (requested == KERNEL_SCALAR) return KERNEL_SCALAR;
@@ -524,13 +535,33 @@ lbm_status init_from_device(lbm_ctx *c, const double *e, const double *qx, const
     return LBM_OK;
 }
 
+// One multi-step launch of `steps` steps from buffer src (FP32 storage).
+cudaError_t wave_launch(const lbm_ctx *c, int src, int steps, cudaStream_t s) {
+    return launch_step_wave(steps, (const float *)c->buf[src], (float *)c->buf[1 - src], c->nx,
+                            c->ny, c->bc_x, c->bc_y, make_coef<float>(c), c->wave_rows, s);
+}
+
+// Launches in one captured graph of multi-step launches: an even number (the
+// buffers end where they began) of about graph_chunk steps.
+int wave_graph_launches(const lbm_ctx *c) {
+    const int pairs = c->graph_chunk / (2 * c->wave_steps);
+    return 2 * (pairs > 1 ? pairs : 1);
+}
+
 lbm_status build_graph(lbm_ctx *c, int start) {
     CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     int src = start;
     cudaError_t le = cudaSuccess;
-    for (int s = 0; s < c->graph_chunk && le == cudaSuccess; ++s) {
-        le = dispatch<StepOp>(c, src, c->cap_stream);
-        src = 1 - src;
+    if (c->kernel == KERNEL_WAVE) {
+        for (int s = 0; s < wave_graph_launches(c) && le == cudaSuccess; ++s) {
+            le = wave_launch(c, src, c->wave_steps, c->cap_stream);
+            src = 1 - src;
+        }
+    } else {
+        for (int s = 0; s < c->graph_chunk && le == cudaSuccess; ++s) {
+            le = dispatch<StepOp>(c, src, c->cap_stream);
+            src = 1 - src;
+        }
     }
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
@@ -545,6 +576,128 @@ lbm_status build_graph(lbm_ctx *c, int start) {
         c->graph[start] = nullptr;
         return cuda_fail(c, ie, "cudaGraphInstantiate");
     }
+    return LBM_OK;
+}
+
+// Launch timing: which = 0 multi-step launches, 1 single steps, 2 steps
+// that also reduce the residual.  timed_begin records the opening event of
+// a launch (or returns a null record when timing is off), timed_end the
+// closing one.
+enum { TIMED_WAVE = 0, TIMED_SINGLE = 1, TIMED_RESIDUAL = 2 };
+
+cudaError_t timed_begin(lbm_ctx *c, int which, long steps, int *slot) {
+    *slot = -1;
+    if (!c->timing) return cudaSuccess;
+    lbm_ctx::Timed t{nullptr, nullptr, which, steps};
+    cudaError_t e = cudaEventCreate(&t.a);
+    if (e == cudaSuccess) e = cudaEventCreate(&t.b);
+    if (e == cudaSuccess) e = cudaEventRecord(t.a, c->stream);
+    if (e != cudaSuccess) {
+        if (t.a) cudaEventDestroy(t.a);
+        if (t.b) cudaEventDestroy(t.b);
+        return e;
+    }
+    c->timed.push_back(t);
+    *slot = (int)c->timed.size() - 1;
+    return cudaSuccess;
+}
+
+cudaError_t timed_end(lbm_ctx *c, int slot) {
+    if (slot < 0) return cudaSuccess;
+    return cudaEventRecord(c->timed[slot].b, c->stream);
+}
+
+// Folds the recorded launches into the totals (after the stream is
+// synchronised) and releases their events.
+cudaError_t timed_collect(lbm_ctx *c) {
+    cudaError_t err = cudaSuccess;
+    for (auto &t : c->timed) {
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, t.a, t.b);
+        if (err == cudaSuccess) {
+            c->timed_ms[t.which] += ms;
+            c->timed_launches[t.which] += 1;
+            c->timed_steps[t.which] += t.steps;
+        }
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    c->timed.clear();
+    return err;
+}
+
+lbm_status single_step(lbm_ctx *c) {
+    int slot;
+    CK(c, timed_begin(c, TIMED_SINGLE, 1, &slot));
+    CK(c, dispatch<StepOp>(c, c->cur, c->stream));
+    CK(c, timed_end(c, slot));
+    c->cur = 1 - c->cur;
+    c->n += 1;
+    c->launches += 1;
+    return LBM_OK;
+}
+
+// Advances n steps.  With the multi-step kernel a launch of k steps leaves
+// the post-collision state of its last step only; the read-outs need the one
+// of the step before too (they pull it), so a call that ends readable
+// (end_readable) finishes with a single step, and lbm_step_residual's plain
+// steps end without one, as its own last step is a single step.
+lbm_status advance(lbm_ctx *c, long n, bool end_readable) {
+    if (n <= 0) return LBM_OK;
+    if (c->kernel == KERNEL_RESIDENT) {
+        // all n steps in one launch; the buffers end as n single steps leave them
+        const int last = c->cur ^ (int)(n & 1);
+        CK(c, launch_resident((const float *)c->buf[c->cur], (float *)c->buf[last],
+                              (float *)c->buf[last ^ 1], c->nx, c->ny, c->bc_x, c->bc_y,
+                              make_coef<float>(c), n, c->rplan, status_word(c), c->stream));
+        c->cur = last;
+        c->n += n;
+        c->launches += 1;
+        return LBM_OK;
+    }
+    if (c->kernel == KERNEL_WAVE) {
+        const long tail = end_readable ? 1 : 0;
+        long m = n - tail;
+        const int K = c->wave_steps;
+        const int gl = wave_graph_launches(c);
+        if (!c->timing && c->graph_chunk > 0 && m >= (long)gl * K) {
+            if (!c->graph[c->cur])
+                if (lbm_status s = build_graph(c, c->cur)) return s;
+            while (m >= (long)gl * K) {      // an even number of launches: cur unchanged
+                CK(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+                m -= (long)gl * K;
+                c->n += (long)gl * K;
+                c->launches += gl;
+            }
+        }
+        while (m >= WAVE_MIN_STEPS) {
+            const int k = m >= K ? K : (int)m;
+            int slot;
+            CK(c, timed_begin(c, TIMED_WAVE, k, &slot));
+            CK(c, wave_launch(c, c->cur, k, c->stream));
+            CK(c, timed_end(c, slot));
+            c->cur = 1 - c->cur;
+            m -= k;
+            c->n += k;
+            c->launches += 1;
+        }
+        for (long i = 0; i < m + tail; ++i)
+            if (lbm_status s = single_step(c)) return s;
+        return LBM_OK;
+    }
+    long left = n;
+    if (!c->timing && c->graph_chunk > 0 && left >= c->graph_chunk) {
+        if (!c->graph[c->cur])
+            if (lbm_status s = build_graph(c, c->cur)) return s;
+        while (left >= c->graph_chunk) {
+            CK(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+            left -= c->graph_chunk;
+            c->n += c->graph_chunk;
+            c->launches += c->graph_chunk;
+        }
+    }
+    for (; left > 0; --left)
+        if (lbm_status s = single_step(c)) return s;
     return LBM_OK;
 }
 
@@ -580,6 +733,10 @@ void lbm_destroy(lbm_ctx *c) {
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
     drop_graphs(c);
+    for (auto &t : c->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->owns_buf) {
         cudaFree(c->buf[0]);
@@ -623,36 +780,7 @@ lbm_status lbm_step(lbm_ctx *c, long n) {
     if (!c->initialised) return fail(c, LBM_EINVAL, "lbm_init has not been called");
     if (lbm_status s = check_corners(c)) return s;
     DeviceGuard g(c->device);
-    if (c->kernel == KERNEL_RESIDENT) {
-        // all n steps in one launch; the buffers end as n single steps leave them
-        if (n == 0) return LBM_OK;
-        const int last = c->cur ^ (int)(n & 1);
-        CK(c, launch_resident((const float *)c->buf[c->cur], (float *)c->buf[last],
-                              (float *)c->buf[last ^ 1], c->nx, c->ny, c->bc_x, c->bc_y,
-                              make_coef<float>(c), n, c->rplan, status_word(c), c->stream));
-        c->cur = last;
-        c->n += n;
-        c->launches += 1;
-        return LBM_OK;
-    }
-    long left = n;
-    if (c->graph_chunk > 0 && left >= c->graph_chunk) {
-        if (!c->graph[c->cur])
-            if (lbm_status s = build_graph(c, c->cur)) return s;
-        while (left >= c->graph_chunk) {
-            CK(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
-            left -= c->graph_chunk;
-            c->n += c->graph_chunk;
-            c->launches += c->graph_chunk;
-        }
-    }
-    for (; left > 0; --left) {
-        CK(c, dispatch<StepOp>(c, c->cur, c->stream));
-        c->cur = 1 - c->cur;
-        c->n += 1;
-        c->launches += 1;
-    }
-    return LBM_OK;
+    return advance(c, n, true);
 }
 
 lbm_status lbm_sync(lbm_ctx *c) {
@@ -740,9 +868,13 @@ lbm_status lbm_step_residual(lbm_ctx *c, long n, double *r, double *total_energy
     if (n == 0) return lbm_residual(c, r, total_energy);
     DeviceGuard g(c->device);
     if (lbm_status s = ensure_scratch(c, true)) return s;
-    if (lbm_status s = lbm_step(c, n - 1)) return s;
+    if (lbm_status s = check_corners(c)) return s;
+    if (lbm_status s = advance(c, n - 1, false)) return s;
     int blocks = 0;
+    int slot;
+    CK(c, timed_begin(c, TIMED_RESIDUAL, 1, &slot));
     CK(c, dispatch<StepResidualOp>(c, c->cur, &blocks));
+    CK(c, timed_end(c, slot));
     c->cur = 1 - c->cur;
     c->n += 1;
     c->launches += 1;
@@ -823,7 +955,7 @@ long lbm_step_count(const lbm_ctx *c) { return c ? c->n : -1; }
 
 lbm_status lbm_set_kernel(lbm_ctx *c, int kernel) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
-    if (kernel < KERNEL_AUTO || kernel > KERNEL_RESIDENT)
+    if (kernel < KERNEL_AUTO || kernel > KERNEL_WAVE)
         return fail(c, LBM_EINVAL, "unknown kernel");
     const int k = resolve_kernel(c, kernel);
     if (k < 0) return fail(c, LBM_EUNSUPPORTED, "kernel cannot run this lattice");
@@ -937,8 +1069,8 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
     if (trial_steps & 1) ++trial_steps;       // even: the buffers end where they began
     DeviceGuard g(c->device);
     if (lbm_status s = ensure_scratch(c, false)) return s;   // the status word
-    struct Cand { int kernel, stages, cw; };
-    Cand cands[8];
+    struct Cand { int kernel, stages, cw; };   // wave: stages = steps, cw = segment rows
+    Cand cands[16];
     int nc = 0;
     const bool sides = has_sides(c);      // the per-side rules: scalar and vector kernels
     if (c->nx % vector_width(c->precision) == 0) cands[nc++] = {KERNEL_VECTOR, 0, 0};
@@ -947,6 +1079,10 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
         if (!sides && staged_supported(c->precision, c->nx, c->ny, cw))
             for (int st : {2, 3}) cands[nc++] = {KERNEL_STAGED, st, cw};
     if (resident_ok(c)) cands[nc++] = {KERNEL_RESIDENT, 0, 0};
+    if (wave_supported(c->precision, c->nx, c->ny, c->bc_x, c->bc_y) && c->nx >= 128 &&
+        c->ny >= 64)
+        for (int ks : {4, 5, 6})
+            for (int rows : {64, 128}) cands[nc++] = {KERNEL_WAVE, ks, rows};
 
     // keep the state: copy both buffers aside when the lattice holds one
     void *saved = nullptr;
@@ -958,6 +1094,7 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
     }
     const int old_kernel = c->kernel;
     const StagedPlan old_plan = c->plan;
+    const int old_ws = c->wave_steps, old_wr = c->wave_rows;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t err = cudaEventCreate(&e0);
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
@@ -973,7 +1110,21 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
         }
         c->kernel = cands[i].kernel;
         c->plan = p;
-        if (c->kernel == KERNEL_RESIDENT) {
+        long steps_timed = trial_steps;
+        if (c->kernel == KERNEL_WAVE) {
+            // its point is several steps per launch: time whole launches, an
+            // even number (the buffers end where they began)
+            c->wave_steps = cands[i].stages;
+            c->wave_rows = cands[i].cw;
+            int launches = (trial_steps + c->wave_steps - 1) / c->wave_steps;
+            launches += launches & 1;
+            steps_timed = (long)launches * c->wave_steps;
+            for (int s = 0; s < 2 && err == cudaSuccess; ++s)      // warm-up
+                err = wave_launch(c, s & 1, c->wave_steps, c->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+            for (int s = 0; s < launches && err == cudaSuccess; ++s)
+                err = wave_launch(c, s & 1, c->wave_steps, c->stream);
+        } else if (c->kernel == KERNEL_RESIDENT) {
             // its point is many steps per launch: time one launch of them all
             const Coef<float> kf = make_coef<float>(c);
             float *b0 = (float *)c->buf[0], *b1 = (float *)c->buf[1];
@@ -994,12 +1145,15 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
         if (err == cudaSuccess) err = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        ms = ms * (float)trial_steps / (float)steps_timed;      // per trial_steps steps
         if (err == cudaSuccess && (best_i < 0 || ms < best)) {
             best = ms;
             best_i = i;
             best_plan = p;
         }
     }
+    c->wave_steps = old_ws;
+    c->wave_rows = old_wr;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (saved) {
@@ -1012,6 +1166,8 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
     if (err != cudaSuccess || best_i < 0) {
         c->kernel = old_kernel;
         c->plan = old_plan;
+        c->wave_steps = old_ws;
+        c->wave_rows = old_wr;
         return err != cudaSuccess ? cuda_fail(c, err, "lbm_autotune")
                                   : fail(c, LBM_ECUDA, "no kernel could be timed");
     }
@@ -1019,6 +1175,10 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
     drop_graphs(c);
     c->kernel = cands[best_i].kernel;
     c->plan = best_plan;
+    if (cands[best_i].kernel == KERNEL_WAVE) {
+        c->wave_steps = cands[best_i].stages;
+        c->wave_rows = cands[best_i].cw;
+    }
     if (cands[best_i].kernel == KERNEL_STAGED) {
         c->stages_req = cands[best_i].stages;
         c->ctas_req = 0;
@@ -1027,6 +1187,59 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
     }
     if (kernel) *kernel = c->kernel;
     if (us_per_step) *us_per_step = 1000.0 * best / trial_steps;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wave_config(lbm_ctx *c, int steps, int rows) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (steps < WAVE_MIN_STEPS || steps > WAVE_MAX_STEPS)
+        return fail(c, LBM_EINVAL, "steps per launch must be 2..8");
+    if (rows < 1) return fail(c, LBM_EINVAL, "rows per segment must be >= 1");
+    if (steps != c->wave_steps || rows != c->wave_rows) {
+        DeviceGuard g(c->device);
+        drop_graphs(c);
+        c->wave_steps = steps;
+        c->wave_rows = rows;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_wave_config(const lbm_ctx *c, int *steps, int *rows) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (steps) *steps = c->wave_steps;
+    if (rows) *rows = c->wave_rows;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_launch_timing(lbm_ctx *c, int on) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    DeviceGuard g(c->device);
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (auto &t : c->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    c->timed.clear();
+    for (int i = 0; i < 3; ++i) {
+        c->timed_ms[i] = 0.0;
+        c->timed_launches[i] = 0;
+        c->timed_steps[i] = 0;
+    }
+    c->timing = on != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_launch_time(lbm_ctx *c, int which, double *ms, long long *launches,
+                           long long *steps) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (which < LBM_TIMED_WAVE || which > LBM_TIMED_RESIDUAL)
+        return fail(c, LBM_EINVAL, "unknown launch kind");
+    DeviceGuard g(c->device);
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, timed_collect(c));
+    if (ms) *ms = c->timed_ms[which];
+    if (launches) *launches = c->timed_launches[which];
+    if (steps) *steps = c->timed_steps[which];
     return LBM_OK;
 }
 

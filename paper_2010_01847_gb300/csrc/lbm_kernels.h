@@ -19,7 +19,7 @@ struct NvtxRange {
 
 enum { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2, PREC_FP64 = 3 };
 enum { KERNEL_AUTO = 0, KERNEL_SCALAR = 1, KERNEL_VECTOR = 2, KERNEL_STAGED = 3,
-       KERNEL_RESIDENT = 4 };
+       KERNEL_RESIDENT = 4, KERNEL_WAVE = 5 };
 
 // 16-bit storage keeps a plane of tile references after the 8 population
 // planes (refs16.cuh): tiles of 8 nodes when nx is a multiple of 8, else of
@@ -145,6 +145,17 @@ cudaError_t launch_resident(const float *src, float *out_last, float *out_prev, 
                             int bc_x, int bc_y, const Coef<float> &k, long steps,
                             const ResidentPlan &p, int *status, cudaStream_t stream);
 
+// The multi-step kernel (wave.cu): `steps` (WAVE_MIN_STEPS..WAVE_MAX_STEPS)
+// time steps in one launch, src (post-collision, step n) -> dst
+// (post-collision, step n + steps); the post-collision state of step
+// n + steps - 1 is not kept.  Strips of 64 columns, segments of seg_rows rows
+// (clipped to ny).  cudaErrorInvalidValue for lattices it does not take
+// (wave_supported) or src == dst.
+constexpr int WAVE_MIN_STEPS = 2;
+constexpr int WAVE_MAX_STEPS = 8;
+bool wave_supported(int precision, int nx, int ny, int bc_x, int bc_y);
+cudaError_t launch_step_wave(int steps, const float *src, float *dst, int nx, int ny, int bc_x,
+                             int bc_y, const Coef<float> &k, int seg_rows, cudaStream_t stream);
 // Runs the staged kernel's bounded mbarrier wait against a barrier nothing
 // completes (one CTA, ~2 s); the wait gives up and ORs 1 into *status.
 cudaError_t launch_wait_probe(int *status, cudaStream_t stream);

@@ -337,7 +337,9 @@ cudaError_t launch_step(int kernel, const T *src, T *dst, int nx, int ny, int bc
     if (kernel == KERNEL_STAGED && rq) kernel = KERNEL_VECTOR;
     // single steps of a cluster-resident lattice (the residual step) run on
     // the vector kernel when nx allows, else the scalar one
-    if (kernel == KERNEL_RESIDENT) kernel = nx % Pack<T>::V == 0 ? KERNEL_VECTOR : KERNEL_SCALAR;
+    // and so do the single steps of a multi-step (wave) lattice
+    if (kernel == KERNEL_RESIDENT || kernel == KERNEL_WAVE)
+        kernel = nx % Pack<T>::V == 0 ? KERNEL_VECTOR : KERNEL_SCALAR;
     if constexpr (sizeof(T) == 2) {
         // the staged kernel keeps FP32 / FP64 storage only (16-bit storage
         // with tile references runs on the vector kernels)
@@ -409,7 +411,7 @@ long long step_blocks(int kernel, int precision, int nx, int ny, const StagedPla
     const long long plane = (long long)nx * ny;
     (void)plan;
     if (kernel == KERNEL_STAGED) kernel = KERNEL_VECTOR;    // residual steps run there
-    if (kernel == KERNEL_RESIDENT)
+    if (kernel == KERNEL_RESIDENT || kernel == KERNEL_WAVE)
         kernel = nx % vector_width(precision) == 0 ? KERNEL_VECTOR : KERNEL_SCALAR;
     const long long threads = kernel == KERNEL_VECTOR ? plane / vector_width(precision) : plane;
     const int bs = step_block_size(threads);

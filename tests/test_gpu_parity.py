@@ -58,11 +58,13 @@ def _kernel_ok(kernel, nx, precision):
         return precision in ("fp32", "fp64") and nx % (256 * v) == 0
     if kernel == "resident":
         return precision == "fp32"          # every lattice here fits one cluster
+    if kernel == "wave":                    # FP32 storage, node pairs along x
+        return precision == "fp32" and nx % 2 == 0
     return True
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16", "bf16"])
-@pytest.mark.parametrize("kernel", ["scalar", "vector", "staged", "resident", "auto"])
+@pytest.mark.parametrize("kernel", ["scalar", "vector", "staged", "resident", "wave", "auto"])
 @pytest.mark.parametrize("lattice", LATTICES, ids=lambda l: f"{l[0]}x{l[1]}_bc{l[2]}{l[3]}")
 def test_parity_small(lattice, kernel, precision):
     nx, ny, bcx, bcy, de = lattice
@@ -160,10 +162,10 @@ def test_kernels_and_graph_chunks_agree_bitwise(precision, rounding):
     fields = inputs.random_state_fields(nx, ny, seed=5)
     outs = []
     runs = [("scalar", 0), ("vector", 0), ("vector", 64), ("staged", 0), ("staged", 64),
-            ("auto", 16)]
+            ("auto", 16), ("wave", 0), ("wave", 64)]
     for kernel, chunk in runs:
-        if kernel == "staged" and precision != "fp32":
-            continue                      # the staged kernel keeps FP32 / FP64 storage
+        if kernel in ("staged", "wave") and precision != "fp32":
+            continue                      # both keep FP32 (the staged one also FP64) storage
         g = plbm.Lattice(nx, ny, 0.8, 9.0, plbm.PERIODIC_GRADIENT, plbm.DIFFUSE_WALLS, 1e-3,
                          precision=precision, kernel=kernel, graph_chunk=chunk,
                          rounding=rounding)
