@@ -267,7 +267,7 @@ KERNEL_SOURCES = {
                     "pipe16.cu"],
     "step_staged": ["lbm_device.cuh", "mbarrier.cuh", "staged.cu"],
     "step_scalar": ["lbm_device.cuh", "refs16.cuh", "stream_collide.cu"],
-    "step_wave": ["lbm_device.cuh", "wave.cu"],
+    "step_wave": ["lbm_device.cuh", "wave.cuh", "wave.cu"],
 }
 
 
@@ -706,9 +706,10 @@ def run_batch(args):
     t_batch = time.perf_counter() - t0
     updates = float((steps * sites).sum())
     # the plain single-lattice solver, one channel at a time (the fastest
-    # kernel each: cluster-resident up to 16384 nodes, else the vector
-    # kernel in 64-step graphs, the residual fused every check window): all
-    # channels, or a seeded sample with --sequential-sample n > 0
+    # kernel each: cluster-resident up to 16384 nodes, else the one the
+    # autotuner picks -- multi-step or vector launches -- with the residual
+    # fused every check window): all channels, or a seeded sample with
+    # --sequential-sample n > 0
     if args.sequential_sample > 0:
         rng = np.random.default_rng(5)
         sample = sorted(rng.choice(len(inst), size=min(args.sequential_sample, len(inst)),
@@ -722,6 +723,8 @@ def run_batch(args):
         lat = plbm.Lattice(i["nx"], i["ny"], i["tau_N"], i["tau_R"], i["bc_x"], i["bc_y"],
                            i["delta_e"])
         lat.init(np.ones((i["ny"], i["nx"])))
+        if i["nx"] * i["ny"] > 16384:
+            lat.autotune(20)          # untimed set-up: the fastest kernel for this channel
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         lat.residual()
@@ -749,7 +752,7 @@ def run_batch(args):
                    "rejected_unstable_candidates": rejected,
                    "total_sites": int(sites.sum()), "tol": args.tol,
                    "check_every": args.check_every,
-                   "schedule": b.schedule, "autotune_us_per_step": tune_us},
+                   "schedule": b.schedule, "wave": b.wave, "autotune_us_per_step": tune_us},
         "steps": {"min": int(steps.min()), "median": float(np.median(steps)),
                   "max": int(steps.max()), "all_converged": bool(np.all(r < args.tol))},
         "site_updates": updates, "glups": updates / t_batch / 1e9,
@@ -784,7 +787,8 @@ def steady_state_study(n_train, train_steps, n_test, n_ref, tol, check_every, ma
     t0 = time.perf_counter()
     train = warmstart.channels(n_train, seed=inputs.SEED + 1, nx=warmstart.TRAIN_NX,
                                w_range=w_range)
-    prof, tsteps, tr, t_gen = warmstart.steady_profiles(train, tol, check_every, max_steps)
+    prof, tsteps, tr, t_gen = warmstart.steady_profiles(train, tol, check_every, max_steps,
+                                                        schedule="tune")
     ws = warmstart.WarmStart(seed=0, max_batch=max(512, n_train))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -801,8 +805,11 @@ def steady_state_study(n_train, train_steps, n_test, n_ref, tol, check_every, ma
     torch.cuda.synchronize()
     t_ana = time.perf_counter() - t3
     runs = {}
+    schedule = "tune"           # autotuned on the cold batch, then kept for all three
     for name, start in (("cold", None), ("analytic", ana), ("learned", pred)):
-        steps, r, secs, b = warmstart.solve(test, start, tol, check_every, max_steps)
+        steps, r, secs, b = warmstart.solve(test, start, tol, check_every, max_steps,
+                                            schedule=schedule)
+        schedule = warmstart.schedule_of(b)
         runs[name] = {"seconds": secs, "steps": steps, "r": r, "batch": b}
     ref_set = test[:n_ref]
     t4 = time.perf_counter()
@@ -811,7 +818,7 @@ def steady_state_study(n_train, train_steps, n_test, n_ref, tol, check_every, ma
     sites = np.array([i["nx"] * i["ny"] for i in test], dtype=np.float64)
     out = {"tol": tol, "check_every": check_every,
            "train_instances": len(train), "train_steps": train_steps,
-           "held_out": len(test), "widths": list(w_range)}
+           "held_out": len(test), "widths": list(w_range), "schedule": schedule}
     for name, run in runs.items():
         b = run["batch"]
         ee, eq = warmstart.profile_errors(b.profiles()[:n_ref], ref, ref_set)

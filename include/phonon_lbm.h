@@ -325,7 +325,7 @@ lbm_status lbm_get_staged_config(const lbm_ctx *ctx, int *stages, int *ctas_per_
 /* Autotuner: times every stream-collide kernel and staged shape that can
  * run this lattice (vector or scalar; staged with 2 or 3 stages and 8 or 4
  * consumer warps; cluster-resident; the multi-step kernel with 4, 5 or 6
- * steps per launch and segments of 64 or 128 rows, on lattices of at least
+ * steps per launch and segments of 128 or 256 rows, on lattices of at least
  * 128 x 64 nodes), trial_steps steps each (0 = 20) after 2 warm-up steps,
  * on the context's stream, and keeps the fastest for later lbm_step calls.
  * The timings run on the context's own buffers; when the context holds a
@@ -345,7 +345,7 @@ lbm_status lbm_set_graph_chunk(lbm_ctx *ctx, int steps);
  * launch (2..8) and strips of `rows` rows (>= 1; clipped to ny).  A launch
  * reads and writes the planes once: 64 B per node per `steps` steps, plus
  * the 2 x steps rows of overlap each segment reads.  Each warp keeps about
- * 27 registers per step level (steps = 4: 168 per thread).  Defaults 4 and
+ * 27 registers per step level (steps = 4: 158 per thread).  Defaults 4 and
  * 128; lbm_autotune sets both.  EINVAL out of range. */
 lbm_status lbm_set_wave_config(lbm_ctx *ctx, int steps, int rows);
 lbm_status lbm_get_wave_config(const lbm_ctx *ctx, int *steps, int *rows);
@@ -440,10 +440,23 @@ lbm_status lbm_batch_set_schedule(lbm_batch *batch, int threads_per_item, int ct
 lbm_status lbm_batch_get_schedule(const lbm_batch *batch, int *threads_per_item,
                                   int *ctas_per_sm, int *grid);
 
+/* Multi-step launches for the batch (LBM_FP32 storage, every nx even):
+ * the plain steps of lbm_batch_step and of each lbm_batch_solve window run
+ * `steps` (2..8) time steps per launch, each warp advancing a strip of 64
+ * columns and `rows` rows of one instance in registers (the kernel of
+ * LBM_KERNEL_WAVE, with the instance's coefficients); results bit-identical
+ * to single steps.  steps = 0 (the default): one step per launch.
+ * lbm_batch_step(n) ends with a single step (the read-outs pull from the
+ * buffer the last step read); a solve window ends with its residual step.
+ * EINVAL out of range; EUNSUPPORTED for other storage or an odd nx. */
+lbm_status lbm_batch_set_wave(lbm_batch *batch, int steps, int rows);
+lbm_status lbm_batch_get_wave(const lbm_batch *batch, int *steps, int *rows);
+
 /* Autotuner: times every schedule above (trial_steps steps each, 0 = 10)
- * on the initialised batch, keeps the fastest; the state is copied aside
- * (2 x population bytes of temporary device memory) and restored.
- * Synchronous. */
+ * on the initialised batch and, with LBM_FP32 storage, multi-step launches
+ * of 3 or 4 steps with segments of 64 or 128 rows; keeps the fastest per
+ * step (us_per_step).  The state is copied aside (2 x population bytes of
+ * temporary device memory) and restored.  Synchronous. */
 lbm_status lbm_batch_autotune(lbm_batch *batch, int trial_steps, double *us_per_step);
 
 /* Normalised steady profiles of every instance (all need the periodic

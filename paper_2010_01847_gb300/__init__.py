@@ -51,6 +51,7 @@ EXPORTS = [
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_init", "lbm_batch_step",
     "lbm_batch_residuals", "lbm_batch_solve", "lbm_batch_moments", "lbm_batch_set_schedule",
     "lbm_batch_get_schedule", "lbm_batch_autotune", "lbm_batch_active", "lbm_batch_steps",
+    "lbm_batch_set_wave", "lbm_batch_get_wave",
     "lbm_batch_last_error", "lbm_batch_profiles", "lbm_batch_init_profiles",
     "lbm_analytic_profiles",
     "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_param_count", "lbm_mlp_set_params",
@@ -151,6 +152,9 @@ def load_library(path: str = LIB_PATH):
         "lbm_batch_set_schedule": (st, [vp, ctypes.c_int, ctypes.c_int]),
         "lbm_batch_get_schedule": (st, [vp] + [ctypes.POINTER(ctypes.c_int)] * 3),
         "lbm_batch_autotune": (st, [vp, ctypes.c_int, dp]),
+        "lbm_batch_set_wave": (st, [vp, ctypes.c_int, ctypes.c_int]),
+        "lbm_batch_get_wave": (st, [vp, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]),
         "lbm_batch_active": (c_long, [vp]),
         "lbm_batch_steps": (c_long, [vp, ctypes.c_int]),
         "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
@@ -641,6 +645,16 @@ class Batch:
         us = ctypes.c_double()
         self._check(self._lib.lbm_batch_autotune(self._b, int(trial_steps), ctypes.byref(us)))
         return us.value
+
+    def set_wave(self, steps, rows=128):
+        """Multi-step launches (lbm_batch_set_wave; steps 0 = one step per launch)."""
+        self._check(self._lib.lbm_batch_set_wave(self._b, int(steps), int(rows)))
+
+    @property
+    def wave(self):
+        v = [ctypes.c_int() for _ in range(2)]
+        self._check(self._lib.lbm_batch_get_wave(self._b, *[ctypes.byref(x) for x in v]))
+        return {"steps": v[0].value, "rows": v[1].value}
 
     def profiles(self):
         """Normalised steady profiles [count, 512] (CUDA float32 tensor)."""

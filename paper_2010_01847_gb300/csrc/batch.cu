@@ -28,6 +28,7 @@
 #include "../../include/phonon_lbm.h"
 #include "lbm_kernels.h"
 #include "vector_pull.cuh"
+#include "wave.cuh"
 
 namespace plbm {
 namespace {
@@ -50,6 +51,11 @@ struct Item {
 
 struct Range {
     int inst, begin, end;   // items [begin, end) of an active instance
+};
+
+// A strip-segment of one instance for the multi-step kernel (wave.cuh).
+struct WItem {
+    int inst, tx, sg;
 };
 
 // Block-wide sum of per-warp values (lane 0 of each warp); reusable inside a
@@ -128,6 +134,38 @@ batch_kernel(const T *__restrict__ src, T *__restrict__ dst,
             warp_flush_residual(loc, acc);
             item_sum5(acc, partials + (size_t)it * 5);
         }
+    }
+}
+
+// Several steps per launch (FP32 storage): each warp marches strip-segments
+// of the running instances (wave.cuh), with the instance's coefficients, a
+// common halo H and rows per segment.  Persistent grid: the item count is
+// read from device memory, so captured launches follow retirements.
+constexpr int BW_WARPS = 4;
+constexpr int BW_SMEM = BW_WARPS * wave::RING_ELEMS * (int)sizeof(float2);
+
+template <int K>
+__global__ void __launch_bounds__(BW_WARPS * 32)
+batch_wave(const float *__restrict__ src, float *__restrict__ dst,
+           const InstDev<float> *__restrict__ inst, const WItem *__restrict__ items,
+           const int *__restrict__ n_items, int halo, int seg_rows) {
+    extern __shared__ float2 bw_ring[];
+    const int count = *n_items;
+    const int warps = gridDim.x * BW_WARPS;
+    float2 *ring = bw_ring + (threadIdx.x >> 5) * wave::RING_ELEMS;
+    for (int it = blockIdx.x * BW_WARPS + (threadIdx.x >> 5); it < count; it += warps) {
+        const WItem w = items[it];
+        const InstDev<float> &I = inst[w.inst];
+        wave::Strip a;
+        a.src = src + I.off;
+        a.dst = dst + I.off;
+        a.plane = I.plane;
+        a.nx = I.nx;
+        a.ny = I.ny;
+        a.bc_x = I.bc_x;
+        a.bc_y = I.bc_y;
+        a.seg_rows = seg_rows;
+        wave::run_strip<K>(a, I.k, w.tx, w.sg, halo, ring);
     }
 }
 
@@ -278,9 +316,16 @@ struct lbm_batch {
     int ctas_per_sm = 0;             // 0 = as many as fit
     int grid = 0;
     int sms = 0;
-    cudaGraphExec_t graph = nullptr;
+    // multi-step launches (FP32): steps per launch (0: one step per launch),
+    // rows per segment, strip-segment items of the running instances
+    int wave_steps = 0;
+    int wave_rows = 128;
+    WItem *dwitems = nullptr, *hwitems = nullptr;
+    long long max_witems = 0;
+    int n_witems = 0;
+    int wave_grid[WAVE_MAX_STEPS + 1] = {0};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // per starting buffer
     int graph_k = 0;
-    int graph_parity = 0;
     std::string err;
 };
 
@@ -381,29 +426,54 @@ cudaError_t upload_table_any(lbm_batch *b) {
     return b->precision == PREC_FP64 ? upload_table<double>(b) : upload_table<float>(b);
 }
 
+// Strip-segments of an instance for the multi-step launches of this batch:
+// halo of the largest launch, strips of 64 - 2 halo columns.
+int wave_halo(const lbm_batch *b) { return wave::halo(b->wave_steps); }
+long long wave_tiles(const lbm_batch *b, const lbm_instance &in) {
+    const int S = wave::stride_of(wave_halo(b));
+    return (in.nx + S - 1) / S;
+}
+long long wave_segs(const lbm_batch *b, const lbm_instance &in) {
+    const int rows = b->wave_rows < in.ny ? b->wave_rows : in.ny;
+    return (in.ny + rows - 1) / rows;
+}
+
 // Items and ranges of the active instances, uploaded for the next launches.
 cudaError_t rebuild_items(lbm_batch *b) {
     const int V = vec_width(b->precision);
-    int ni = 0, nr = 0;
+    int ni = 0, nr = 0, nw = 0;
     for (int i = 0; i < b->count; ++i) {
         if (!b->active[i]) continue;
         const long long threads = (long long)b->inst[i].nx * b->inst[i].ny / V;
         const int begin = ni;
         for (long long f = 0; f < threads; f += b->tpi) b->hitems[ni++] = Item{i, (int)f};
         b->hranges[nr++] = Range{i, begin, ni};
+        if (b->wave_steps > 0) {
+            // strips of one segment next to each other (their halo columns
+            // are read from L2 by both)
+            const long long tiles = wave_tiles(b, b->inst[i]), segs = wave_segs(b, b->inst[i]);
+            for (long long sg = 0; sg < segs; ++sg)
+                for (long long tx = 0; tx < tiles; ++tx)
+                    b->hwitems[nw++] = WItem{i, (int)tx, (int)sg};
+        }
     }
     b->n_items = ni;
     b->n_ranges = nr;
+    b->n_witems = nw;
     b->hcounts[0] = ni;
     b->hcounts[1] = nr;
+    b->hcounts[2] = nw;
     cudaError_t e = cudaSuccess;
     if (ni) e = cudaMemcpyAsync(b->ditems, b->hitems, sizeof(Item) * ni, cudaMemcpyHostToDevice,
                                 b->stream);
     if (e == cudaSuccess && nr)
         e = cudaMemcpyAsync(b->dranges, b->hranges, sizeof(Range) * nr, cudaMemcpyHostToDevice,
                             b->stream);
+    if (e == cudaSuccess && nw)
+        e = cudaMemcpyAsync(b->dwitems, b->hwitems, sizeof(WItem) * nw, cudaMemcpyHostToDevice,
+                            b->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->dcounts, b->hcounts, 2 * sizeof(int), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(b->dcounts, b->hcounts, 3 * sizeof(int), cudaMemcpyHostToDevice,
                             b->stream);
     // the host staging arrays are reused by the next rebuild: wait here
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -439,6 +509,62 @@ cudaError_t launch_any(lbm_batch *b, int mode, int src, cudaStream_t s) {
     }
 }
 
+template <int K>
+cudaError_t launch_wave_k(lbm_batch *b, int src, cudaStream_t s) {
+    if (!b->wave_grid[K]) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_wave<K>,
+                                                                      BW_WARPS * 32, BW_SMEM);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        b->wave_grid[K] = b->sms * per_sm;
+    }
+    batch_wave<K><<<b->wave_grid[K], BW_WARPS * 32, BW_SMEM, s>>>(
+        (const float *)b->buf[src], (float *)b->buf[1 - src], (const InstDev<float> *)b->dinst,
+        b->dwitems, b->dcounts + 2, wave_halo(b), b->wave_rows);
+    return cudaGetLastError();
+}
+
+// One multi-step launch of k steps (2 <= k <= wave_steps) from buffer src.
+cudaError_t launch_wave(lbm_batch *b, int k, int src, cudaStream_t s) {
+    switch (k) {
+        case 2: return launch_wave_k<2>(b, src, s);
+        case 3: return launch_wave_k<3>(b, src, s);
+        case 4: return launch_wave_k<4>(b, src, s);
+        case 5: return launch_wave_k<5>(b, src, s);
+        case 6: return launch_wave_k<6>(b, src, s);
+        case 7: return launch_wave_k<7>(b, src, s);
+        default: return launch_wave_k<8>(b, src, s);
+    }
+}
+
+// Steps of the next launch when m plain steps are left: up to wave_steps
+// in one multi-step launch, one for a remainder of one (or without them).
+int next_launch_steps(const lbm_batch *b, long m) {
+    if (b->wave_steps >= WAVE_MIN_STEPS && m >= WAVE_MIN_STEPS)
+        return (int)(m < b->wave_steps ? m : b->wave_steps);
+    return 1;
+}
+
+// Launches n plain steps take (the buffers swap once per launch).
+long plain_launches(const lbm_batch *b, long n) {
+    long count = 0;
+    for (long m = n; m > 0; m -= next_launch_steps(b, m)) ++count;
+    return count;
+}
+
+// n plain steps from buffer *src (which follows the launches).
+cudaError_t plain_steps(lbm_batch *b, long n, int *src, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (long m = n; m > 0 && e == cudaSuccess;) {
+        const int k = next_launch_steps(b, m);
+        e = k == 1 ? launch_any(b, B_STEP, *src, s) : launch_wave(b, k, *src, s);
+        *src = 1 - *src;
+        m -= k;
+    }
+    return e;
+}
+
 cudaError_t launch_finalize_batch(lbm_batch *b, cudaStream_t s) {
     batch_finalize<<<b->count, 128, 0, s>>>(b->partials, b->dranges, b->dcounts + 1, b->dsums);
     return cudaGetLastError();
@@ -466,8 +592,10 @@ cudaError_t plan_grid(lbm_batch *b) {
 }
 
 void drop_graph(lbm_batch *b) {
-    if (b->graph) cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+        b->graph[i] = nullptr;
+    }
     b->graph_k = 0;
 }
 
@@ -574,6 +702,19 @@ lbm_status lbm_batch_create(const lbm_instance *inst, int count, lbm_precision p
     if (e == cudaSuccess) e = cudaMallocHost(&b->hitems, sizeof(Item) * b->max_items);
     if (e == cudaSuccess) e = cudaMallocHost(&b->hranges, sizeof(Range) * count);
     if (e == cudaSuccess) e = cudaMallocHost(&b->hcounts, 4 * sizeof(int));
+    if (e == cudaSuccess) {
+        // strip-segments of the smallest strips and segments a batch may use
+        long long nw = 0;
+        for (int i = 0; i < count; ++i) {
+            const int S = wave::stride_of(wave::halo(WAVE_MAX_STEPS));
+            nw += (long long)((inst[i].nx + S - 1) / S) * inst[i].ny;
+        }
+        b->max_witems = nw;
+        if (precision == PREC_FP32) {
+            e = cudaMalloc(&b->dwitems, sizeof(WItem) * nw);
+            if (e == cudaSuccess) e = cudaMallocHost(&b->hwitems, sizeof(WItem) * nw);
+        }
+    }
     if (e != cudaSuccess) return bail(bcuda(nullptr, e, "lbm_batch_create allocation"));
     e = plan_grid(b);
     if (e != cudaSuccess) return bail(bcuda(nullptr, e, "lbm_batch_create occupancy"));
@@ -601,6 +742,8 @@ void lbm_batch_destroy(lbm_batch *b) {
     cudaFreeHost(b->hitems);
     cudaFreeHost(b->hranges);
     cudaFreeHost(b->hcounts);
+    cudaFree(b->dwitems);
+    cudaFreeHost(b->hwitems);
     delete b;
 }
 
@@ -706,7 +849,10 @@ lbm_status lbm_batch_step(lbm_batch *b, long n) {
     if (n < 0) return bfail(b, LBM_EINVAL, "n must be >= 0");
     if (!b->initialised) return bfail(b, LBM_EINVAL, "lbm_batch_init has not been called");
     BGuard g(b->device);
-    for (long s = 0; s < n; ++s) {
+    if (n > 0) {
+        // the read-outs pull the state from the buffer the last step read,
+        // which a multi-step launch does not leave: end with a single step
+        BCK(b, plain_steps(b, n - 1, &b->cur, b->stream));
         BCK(b, launch_any(b, B_STEP, b->cur, b->stream));
         b->cur = 1 - b->cur;
     }
@@ -759,16 +905,17 @@ lbm_status lbm_batch_solve(lbm_batch *b, double tol, int check_every, long max_s
         return bfail(b, LBM_EINVAL, "check_every must be an even number >= 2");
     if (max_steps < 0) return bfail(b, LBM_EINVAL, "max_steps must be >= 0");
     BGuard g(b->device);
-    // a window has an even number of steps, so it ends on the buffer parity
-    // it started with; the graph is captured for the current parity
-    if (!b->graph || b->graph_k != check_every || b->graph_parity != b->cur) {
-        drop_graph(b);
+    // one captured graph per starting buffer: check_every - 1 plain steps
+    // (multi-step launches when set), then the step with the residual sums
+    if (b->graph_k != check_every) drop_graph(b);
+    const long window_launches = plain_launches(b, check_every - 1) + 1;
+    for (int start = 0; start < 2; ++start) {
+        if (b->graph[start]) continue;
         cudaStream_t cap = nullptr;
         BCK(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        int src = b->cur;
-        for (int s = 0; s < check_every - 1 && e == cudaSuccess; ++s, src = 1 - src)
-            e = launch_any(b, B_STEP, src, cap);
+        int src = start;
+        if (e == cudaSuccess) e = plain_steps(b, check_every - 1, &src, cap);
         // have_prev is a launch argument: capture the comparing variant;
         // the first window's comparison is ignored (no history yet)
         const bool hp = b->have_prev;
@@ -783,15 +930,15 @@ lbm_status lbm_batch_solve(lbm_batch *b, double tol, int check_every, long max_s
         cudaError_t ee = cudaStreamEndCapture(cap, &gr);
         cudaStreamDestroy(cap);
         if (e == cudaSuccess) e = ee;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, gr, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[start], gr, 0);
         if (gr) cudaGraphDestroy(gr);
         if (e != cudaSuccess) {
-            b->graph = nullptr;
+            b->graph[start] = nullptr;
             return bcuda(b, e, "batch window capture");
         }
         b->graph_k = check_every;
-        b->graph_parity = b->cur;
     }
+
     bool bad = false;
     while (true) {
         bool any = false;
@@ -805,8 +952,9 @@ lbm_status lbm_batch_solve(lbm_batch *b, double tol, int check_every, long max_s
                 changed = true;
             }
         if (changed) BCK(b, rebuild_items(b));
-        BCK(b, cudaGraphLaunch(b->graph, b->stream));
+        BCK(b, cudaGraphLaunch(b->graph[b->cur], b->stream));
         BCK(b, cudaStreamSynchronize(b->stream));
+        if (window_launches & 1) b->cur = 1 - b->cur;
         changed = false;
         for (int i = 0; i < b->count; ++i) {
             if (!b->active[i]) continue;
@@ -968,6 +1116,43 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, double *us_per_step
         }
         if (err != cudaSuccess) break;
     }
+    // multi-step launches (FP32): per-step time of launches of K steps with
+    // the best single-step schedule for the other launches
+    const int old_ws = b->wave_steps, old_wr = b->wave_rows;
+    int best_ws = 0, best_wr = old_wr;
+    float best_step = best / trial_steps;      // ms per step of the single steps
+    if (err == cudaSuccess && b->precision == PREC_FP32 && b->dwitems) {
+        b->tpi = best_t;
+        b->ctas_per_sm = best_c;
+        if (plan_grid(b) != cudaSuccess) (void)cudaGetLastError();
+        for (int ks : {3, 4}) {
+            for (int rows : {64, 128}) {
+                b->wave_steps = ks;
+                b->wave_rows = rows;
+                if ((err = rebuild_items(b)) != cudaSuccess) break;
+                const int launches = 2 * ((trial_steps + 2 * ks - 1) / (2 * ks));
+                for (int s = 0; s < 2 && err == cudaSuccess; ++s)
+                    err = launch_wave(b, ks, s & 1, b->stream);
+                if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+                for (int s = 0; s < launches && err == cudaSuccess; ++s)
+                    err = launch_wave(b, ks, s & 1, b->stream);
+                if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                if (err != cudaSuccess) break;
+                const float per_step = ms / (launches * ks);
+                if (per_step < best_step) {
+                    best_step = per_step;
+                    best_ws = ks;
+                    best_wr = rows;
+                }
+            }
+            if (err != cudaSuccess) break;
+        }
+    }
+    b->wave_steps = err == cudaSuccess ? best_ws : old_ws;
+    b->wave_rows = err == cudaSuccess ? best_wr : old_wr;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (int i = 0; i < 2 && err == cudaSuccess; ++i)
@@ -982,7 +1167,34 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, double *us_per_step
     if (err == cudaSuccess) err = pe;
     if (err == cudaSuccess) err = rebuild_items(b);
     if (err != cudaSuccess) return bcuda(b, err, "lbm_batch_autotune");
-    if (us_per_step) *us_per_step = best >= 0.f ? 1000.0 * best / trial_steps : 0.0;
+    if (us_per_step) *us_per_step = best >= 0.f ? 1000.0 * best_step : 0.0;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_wave(lbm_batch *b, int steps, int rows) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (steps != 0 && (steps < WAVE_MIN_STEPS || steps > WAVE_MAX_STEPS))
+        return bfail(b, LBM_EINVAL, "steps per launch must be 0 or 2..8");
+    if (rows < 1) return bfail(b, LBM_EINVAL, "rows per segment must be >= 1");
+    if (steps && b->precision != PREC_FP32)
+        return bfail(b, LBM_EUNSUPPORTED, "multi-step launches need LBM_FP32 storage");
+    if (steps) {
+        for (int i = 0; i < b->count; ++i)
+            if (b->inst[i].nx % 2)
+                return bfail(b, LBM_EUNSUPPORTED, "multi-step launches need even nx");
+    }
+    BGuard g(b->device);
+    b->wave_steps = steps;
+    b->wave_rows = rows;
+    drop_graph(b);
+    if (b->initialised) BCK(b, rebuild_items(b));
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_wave(const lbm_batch *b, int *steps, int *rows) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (steps) *steps = b->wave_steps;
+    if (rows) *rows = b->wave_rows;
     return LBM_OK;
 }
 

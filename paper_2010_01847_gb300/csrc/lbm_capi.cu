@@ -1082,7 +1082,7 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
     if (wave_supported(c->precision, c->nx, c->ny, c->bc_x, c->bc_y) && c->nx >= 128 &&
         c->ny >= 64)
         for (int ks : {4, 5, 6})
-            for (int rows : {64, 128}) cands[nc++] = {KERNEL_WAVE, ks, rows};
+            for (int rows : {128, 256}) cands[nc++] = {KERNEL_WAVE, ks, rows};
 
     // keep the state: copy both buffers aside when the lattice holds one
     void *saved = nullptr;

@@ -57,11 +57,29 @@ def features(instances):
     return (2.0 * (raw - lo) / (hi - lo) - 1.0).astype(np.float32)
 
 
-def steady_profiles(instances, tol=1e-8, check_every=100, max_steps=400000):
+def _schedule(b, schedule):
+    """Applies a batch schedule (None: the defaults; "tune": the autotuner,
+    on the initialised batch; or a dict from schedule_of) before a solve."""
+    if schedule == "tune":
+        b.autotune(10)
+    elif schedule:
+        b.set_schedule(schedule["threads_per_item"], schedule["ctas_per_sm"])
+        b.set_wave(schedule["wave_steps"], schedule["wave_rows"])
+
+
+def schedule_of(b):
+    """The schedule a batch runs with (to repeat it on another batch)."""
+    s, w = b.schedule, b.wave
+    return {"threads_per_item": s["threads_per_item"], "ctas_per_sm": s["ctas_per_sm"],
+            "wave_steps": w["steps"], "wave_rows": w["rows"]}
+
+
+def steady_profiles(instances, tol=1e-8, check_every=100, max_steps=400000, schedule=None):
     """Solve every instance to steady state (cold start) with the batched
     solver and return (profiles [n, 512] CUDA tensor, steps, seconds)."""
     b = Batch(instances)
     b.init()
+    _schedule(b, schedule)
     t0 = time.perf_counter()
     steps, r = b.solve(tol, check_every, max_steps)
     dt = time.perf_counter() - t0
@@ -100,15 +118,18 @@ class WarmStart:
         return _analytic(instances, out, op=1)
 
 
-def solve(instances, profiles=None, tol=1e-8, check_every=100, max_steps=400000):
+def solve(instances, profiles=None, tol=1e-8, check_every=100, max_steps=400000,
+          schedule=None):
     """Batched solve from the cold start (profiles None) or from profiles
-    (predicted, or analytic_profiles); returns (steps, final residuals,
-    seconds, batch)."""
+    (predicted, or analytic_profiles), with a schedule (see _schedule; set
+    up before the timed solve); returns (steps, final residuals, seconds,
+    batch)."""
     b = Batch(instances)
     if profiles is None:
         b.init()
     else:
         b.init_profiles(profiles)
+    _schedule(b, schedule)
     t0 = time.perf_counter()
     steps, r = b.solve(tol, check_every, max_steps)
     return steps, r, time.perf_counter() - t0, b

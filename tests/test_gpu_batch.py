@@ -199,3 +199,52 @@ def test_full_512_channel_batch_in_bench_configuration():
             assert np.array_equal(x, y), k
         lat.close()
     b.close()
+
+
+# --- multi-step launches (lbm_batch_set_wave) -------------------------------
+WAVE_MIXED = [dict(i) for i in MIXED] + [
+    dict(nx=132, ny=21, tau_N=0.9, tau_R=4.0, bc_x=G, bc_y=W, delta_e=1e-3)]   # ragged strips
+
+
+@pytest.mark.parametrize("steps,rows", [(2, 7), (3, 64), (4, 128), (8, 5)])
+def test_batch_wave_equals_single_steps_bitwise(steps, rows):
+    """Multi-step launches of every instance (uneven sizes, both boundary
+    kinds, strips that wrap and ragged last strips) give the single-step
+    batch's states bit for bit, through steps, residuals and a solve."""
+    fields = _fields(WAVE_MIXED, 17)
+    args = [list(x) for x in zip(*fields)]
+    a = plbm.Batch(WAVE_MIXED)
+    a.init(*args)
+    b = plbm.Batch(WAVE_MIXED)
+    b.set_wave(steps, rows)
+    assert b.wave == {"steps": steps, "rows": rows}
+    b.init(*args)
+    for n in (1, 2, 37):
+        a.step(n)
+        b.step(n)
+        for k in range(len(WAVE_MIXED)):
+            for x, y in zip(a.moments(k), b.moments(k)):
+                assert np.array_equal(x, y), (n, k)
+    ra, ea = a.residuals()
+    rb, eb = b.residuals()
+    assert np.array_equal(ea, eb)
+    sa, ra = a.solve(tol=1e-3, check_every=26, max_steps=260)
+    sb, rb = b.solve(tol=1e-3, check_every=26, max_steps=260)
+    assert np.array_equal(sa, sb) and np.array_equal(ra, rb)
+    for k in range(len(WAVE_MIXED)):
+        for x, y in zip(a.moments(k), b.moments(k)):
+            assert np.array_equal(x, y), ("solve", k)
+
+
+def test_batch_wave_refusals():
+    b = plbm.Batch(MIXED, precision="fp16")
+    with pytest.raises(plbm.LBMError) as ex:
+        b.set_wave(4)
+    assert ex.value.status == plbm.EUNSUPPORTED
+    c = plbm.Batch(MIXED)
+    for steps, rows in ((1, 64), (9, 64), (4, 0)):
+        with pytest.raises(plbm.LBMError) as ex:
+            c.set_wave(steps, rows)
+        assert ex.value.status == plbm.EINVAL
+    c.set_wave(0)
+    assert c.wave["steps"] == 0
