@@ -165,7 +165,7 @@ batch_wave(const float *__restrict__ src, float *__restrict__ dst,
         a.bc_x = I.bc_x;
         a.bc_y = I.bc_y;
         a.seg_rows = seg_rows;
-        wave::run_strip<K>(a, I.k, w.tx, w.sg, halo, ring);
+        wave::run_strip<K, true>(a, I.k, w.tx, w.sg, halo, ring);
     }
 }
 

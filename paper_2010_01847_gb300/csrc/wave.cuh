@@ -96,8 +96,9 @@ __device__ __forceinline__ void stage_row(float2 *ring, const Strip &a, int xa, 
     cp_commit();
 }
 
-// One march position s with s - s_lo = P (mod 3).
-template <int K, int P>
+// One march position s with s - s_lo = P (mod 3).  SEAM: some lane of the
+// warp pulls across the seam of a gradient lattice (else no jump is added).
+template <int K, int P, bool SEAM>
 __device__ __forceinline__ void march_step(March<K> &m, const Strip &a, const Coef<float> &k,
                                            int s, int xa, bool out_lane, bool seam_a,
                                            bool seam_b, bool walls, int y0, int y1,
@@ -131,11 +132,11 @@ __device__ __forceinline__ void march_step(March<K> &m, const Strip &a, const Co
             const float jw = i < 4 ? k.jump_axis : k.jump_diag;
             if (cx > 0) {        // node a from the left lane's node b, node b from node a
                 float left = __shfl_up_sync(0xffffffffu, v.y, 1);
-                if (seam_a) left = left + jw;                    // Eq. 59
+                if (SEAM && seam_a) left = left + jw;            // Eq. 59
                 d[i] = make_float2(left, v.x);
             } else if (cx < 0) { // node b from the right lane's node a, node a from node b
                 float right = __shfl_down_sync(0xffffffffu, v.x, 1);
-                if (seam_b) right = right - jw;                  // Eq. 60
+                if (SEAM && seam_b) right = right - jw;          // Eq. 60
                 d[i] = make_float2(v.y, right);
             } else {
                 d[i] = v;
@@ -160,9 +161,11 @@ __device__ __forceinline__ void march_step(March<K> &m, const Strip &a, const Co
 // The march of strip tx (columns tx S - H .. tx S + 63 - H, wrapped,
 // S = 64 - 2H), segment sg (rows sg seg_rows ..) of lattice a: K steps from
 // a.src into a.dst.  H: the halo, even and >= K (a batch keeps one strip
-// layout for launches of fewer steps).  Every lane of the warp calls it
-// (shuffles); warp_ring is the warp's RING_ELEMS float2 of shared memory.
-template <int K>
+// layout for launches of fewer steps).  SEAM: the lattice has the seam
+// gradient (without it no jump is added: fewer instructions per level).
+// Every lane of the warp calls it (shuffles); warp_ring is the warp's
+// RING_ELEMS float2 of shared memory.
+template <int K, bool SEAM>
 __device__ __forceinline__ void run_strip(const Strip &a, const Coef<float> &k, int tx, int sg,
                                           int H, float2 *warp_ring) {
     const int S = stride_of(H);
@@ -200,16 +203,16 @@ __device__ __forceinline__ void run_strip(const Strip &a, const Coef<float> &k, 
     // a position, so no slot keeps a value past its third position
     int s = s_lo;
     for (; s + 2 <= s_end; s += 3) {
-        march_step<K, 0>(m, a, k, s, xa, out_lane, seam_a, seam_b, walls, y0, y1, s_lo, s_load_hi);
-        march_step<K, 1>(m, a, k, s + 1, xa, out_lane, seam_a, seam_b, walls, y0, y1,
+        march_step<K, 0, SEAM>(m, a, k, s, xa, out_lane, seam_a, seam_b, walls, y0, y1, s_lo, s_load_hi);
+        march_step<K, 1, SEAM>(m, a, k, s + 1, xa, out_lane, seam_a, seam_b, walls, y0, y1,
                          s_lo, s_load_hi);
-        march_step<K, 2>(m, a, k, s + 2, xa, out_lane, seam_a, seam_b, walls, y0, y1,
+        march_step<K, 2, SEAM>(m, a, k, s + 2, xa, out_lane, seam_a, seam_b, walls, y0, y1,
                          s_lo, s_load_hi);
     }
     if (s <= s_end)
-        march_step<K, 0>(m, a, k, s, xa, out_lane, seam_a, seam_b, walls, y0, y1, s_lo, s_load_hi);
+        march_step<K, 0, SEAM>(m, a, k, s, xa, out_lane, seam_a, seam_b, walls, y0, y1, s_lo, s_load_hi);
     if (s + 1 <= s_end)
-        march_step<K, 1>(m, a, k, s + 1, xa, out_lane, seam_a, seam_b, walls, y0, y1,
+        march_step<K, 1, SEAM>(m, a, k, s + 1, xa, out_lane, seam_a, seam_b, walls, y0, y1,
                          s_lo, s_load_hi);
     cp_wait<0>();          // nothing of this march left in flight
 }
