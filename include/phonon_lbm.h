@@ -123,9 +123,11 @@ typedef enum {
 /* Which stream-collide kernel lbm_step launches. */
 typedef enum {
     LBM_KERNEL_AUTO = 0,     /* up to 16384 nodes: resident for LBM_FP32,     */
-                             /* scalar for LBM_FP64; else vector when nx      */
-                             /* allows, else scalar (lbm_autotune times the   */
-                             /* candidates)                                   */
+                             /* scalar for LBM_FP64; from 2^24 nodes (nx >=   */
+                             /* 256) wave for LBM_FP32 where it applies (4    */
+                             /* steps per launch, 256-row segments); else     */
+                             /* vector when nx allows, else scalar            */
+                             /* (lbm_autotune times the candidates)           */
     LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx                   */
     LBM_KERNEL_VECTOR = 2,   /* 16-byte vectors along x; nx % (16/size) == 0  */
     LBM_KERNEL_STAGED = 3,   /* bulk asynchronous copies (TMA engine) of row  */

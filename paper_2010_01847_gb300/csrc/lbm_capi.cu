@@ -340,6 +340,7 @@ lbm_status finish_residual(lbm_ctx *c, const double (&sums)[5], double *r,
 }
 
 constexpr long long RESIDENT_AUTO_NODES = 16384;
+constexpr long long WAVE_AUTO_NODES = 1LL << 24;
 
 // Works out the cluster-resident plan (FP32 lattices whose two buffers fit
 // in one cluster's shared memory); false when there is none.
@@ -390,10 +391,19 @@ int resolve_kernel(lbm_ctx *c, int requested) {
         else (void)cudaGetLastError();
     }
     if (requested == KERNEL_AUTO) {
-        // without timing (lbm_autotune times them): the vector kernel, the
-        // fastest measured at 8192^2 for every storage kind (FP32 6.7, 16-bit
-        // 6.5 TB/s against the staged kernel's 5.7 and 6.0), and with the
-        // least set-up for small, launch-latency bound lattices
+        // without timing (lbm_autotune times them): large FP32 lattices the
+        // multi-step kernel (4 steps per launch, 256-row segments: 320
+        // against 106 GLUPS at 8192^2; from 16 M nodes its strip-segments
+        // fill the GPU), else the vector kernel, the fastest single-step
+        // kernel measured at 8192^2 for every storage kind (FP32 6.7, 16-bit
+        // 6.5 TB/s against the staged kernel's 5.7 and 6.0), with the least
+        // set-up for small, launch-latency bound lattices
+        if (c->plane >= WAVE_AUTO_NODES && c->nx >= 256 &&
+            wave_supported(c->precision, c->nx, c->ny, c->bc_x, c->bc_y)) {
+            c->wave_steps = 4;
+            c->wave_rows = 256;
+            return KERNEL_WAVE;
+        }
         return vec_ok ? KERNEL_VECTOR : KERNEL_SCALAR;
     }
     if (requested == KERNEL_VECTOR && !vec_ok) return -1;

@@ -178,25 +178,29 @@ def test_kernels_and_graph_chunks_agree_bitwise(precision, rounding):
 
 
 # --- the named workloads, full runs --------------------------------------
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_poiseuille_128x32_full(precision):
+@pytest.mark.parametrize("precision,kernel", [("fp64", "auto"), ("fp32", "auto"),
+                                              ("fp32", "wave")])
+def test_poiseuille_128x32_full(precision, kernel):
     w = inputs.POISEUILLE_128x32
     tau_N, tau_R = tau_pair(w.kn_N, w.kn_R, w.length)
     fields = inputs.initial_fields(w)
-    g = gpu_run(w.nx, w.ny, tau_N, tau_R, fields, w.steps, w.bc_x, w.bc_y, w.delta_e, precision)
+    g = gpu_run(w.nx, w.ny, tau_N, tau_R, fields, w.steps, w.bc_x, w.bc_y, w.delta_e, precision,
+                kernel)
     o = oracle_run(w.nx, w.ny, tau_N, tau_R, fields, w.steps, w.bc_x, w.bc_y, w.delta_e)
     err_e, err_q = err_metrics(g.moments(), o.moments())
     assert err_e <= TOL[precision] and err_q <= TOL[precision], (err_e, err_q)
 
 
 @pytest.mark.parametrize("kn_R", [0.1, 1.0, 10.0])
-@pytest.mark.parametrize("precision,rounding", [("fp32", "nearest"), ("fp16", "nearest"),
-                                                ("bf16", "stochastic")])
-def test_second_sound_4096x4_full(kn_R, precision, rounding):
+@pytest.mark.parametrize("precision,rounding,kernel", [
+    ("fp32", "nearest", "auto"), ("fp32", "nearest", "wave"), ("fp16", "nearest", "auto"),
+    ("bf16", "stochastic", "auto")])
+def test_second_sound_4096x4_full(kn_R, precision, rounding, kernel):
     w = inputs.second_sound_4096x4(kn_R)
     tau_N, tau_R = tau_pair(w.kn_N, w.kn_R, w.length)
     fields = inputs.initial_fields(w)
-    g = plbm.Lattice(w.nx, w.ny, tau_N, tau_R, precision=precision, rounding=rounding)
+    g = plbm.Lattice(w.nx, w.ny, tau_N, tau_R, precision=precision, rounding=rounding,
+                     kernel=kernel)
     g.init(*fields)
     g.step(w.steps)
     o = oracle_run(w.nx, w.ny, tau_N, tau_R, fields, w.steps)
@@ -429,17 +433,23 @@ def test_device_init_matches_host_init():
 
 
 # --- a lattice whose plane offsets pass 2^31 elements ------------------------
-def test_64bit_offsets_light_cone():
+@pytest.mark.parametrize("kernel", ["vector", "wave"])
+def test_64bit_offsets_light_cone(kernel):
     """20480 x 16384 FP32 (3.4e8 nodes, 21 GB of populations): the upper
     planes start beyond 2^31 elements, so every index must be 64-bit.
     Sampled nodes (the last ones included) after 12 steps against the oracle
-    on periodic light-cone windows."""
+    on periodic light-cone windows; single steps and multi-step launches
+    (the kernel this size gets without the autotuner)."""
     nx, ny, n = 20480, 16384, 12
     assert 7 * nx * ny > 2 ** 31
     tau_N, tau_R = 0.9, 15.0
     e = inputs.sine_mode(nx, ny, 517.0, 1e-3, direction="xy")
-    g = gpu_run(nx, ny, tau_N, tau_R, (e, None, None), n)
-    assert g.kernel == "vector"
+    g = gpu_run(nx, ny, tau_N, tau_R, (e, None, None), n, kernel=kernel)
+    assert g.kernel == kernel
+    if kernel == "wave":
+        auto = plbm.Lattice(nx, ny, tau_N, tau_R, torch_buffers=False)
+        assert auto.kernel == "wave"
+        auto.close()
     ge, gqx, gqy = g.moments_device()
     rng = np.random.default_rng(4)
     pts = [(ny - 1, nx - 1), (ny - 1, nx - 2), (ny - 2, 0), (0, 0), (0, nx - 1)] + \
