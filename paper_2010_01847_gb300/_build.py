@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphonon_lbm.so")
 SOURCES = ["lbm_capi.cu", "stream_collide.cu", "staged.cu", "readout.cu", "noalloc.cu",
-           "batch.cu", "mlp.cu", "lattices.cu", "resident.cu", "pipe16.cu", "wave.cu"]
+           "batch.cu", "mlp.cu", "lattices.cu", "resident.cu", "pipe16.cu", "wave.cu", "wave16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
          "--expt-relaxed-constexpr"]

@@ -371,8 +371,12 @@ int resolve_kernel(lbm_ctx *c, int requested) {
     // 5.3-5.6 against 6.2 us per step)
     if (requested == KERNEL_AUTO && c->precision == PREC_FP64 && c->plane <= RESIDENT_AUTO_NODES)
         return KERNEL_SCALAR;
-    if (requested == KERNEL_WAVE)
-        return wave_supported(c->precision, c->nx, c->ny, c->bc_x, c->bc_y) ? KERNEL_WAVE : -1;
+    if (requested == KERNEL_WAVE) {
+        if (!wave_supported(c->precision, c->nx, c->ny, c->bc_x, c->bc_y)) return -1;
+        if (c->wave_steps > wave_max_steps(c->precision))
+            c->wave_steps = wave_max_steps(c->precision);
+        return KERNEL_WAVE;
+    }
     if (has_sides(c)) {     // the per-side rules: scalar, vector and resident kernels
         if (requested == KERNEL_AUTO) return vec_ok ? KERNEL_VECTOR : KERNEL_SCALAR;
         if (requested == KERNEL_SCALAR) return KERNEL_SCALAR;
@@ -545,10 +549,14 @@ lbm_status init_from_device(lbm_ctx *c, const double *e, const double *qx, const
     return LBM_OK;
 }
 
-// One multi-step launch of `steps` steps from buffer src (FP32 storage).
+// One multi-step launch of `steps` steps from buffer src.
 cudaError_t wave_launch(const lbm_ctx *c, int src, int steps, cudaStream_t s) {
-    return launch_step_wave(steps, (const float *)c->buf[src], (float *)c->buf[1 - src], c->nx,
-                            c->ny, c->bc_x, c->bc_y, make_coef<float>(c), c->wave_rows, s);
+    if (c->precision == PREC_FP32)
+        return launch_step_wave(steps, (const float *)c->buf[src], (float *)c->buf[1 - src],
+                                c->nx, c->ny, c->bc_x, c->bc_y, make_coef<float>(c),
+                                c->wave_rows, s);
+    return launch_step_wave16(c->precision, steps, c->buf[src], c->buf[1 - src], c->nx, c->ny,
+                              c->bc_x, c->bc_y, make_coef<float>(c), c->wave_rows, s);
 }
 
 // Launches in one captured graph of multi-step launches: an even number (the
@@ -1090,9 +1098,15 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
             for (int st : {2, 3}) cands[nc++] = {KERNEL_STAGED, st, cw};
     if (resident_ok(c)) cands[nc++] = {KERNEL_RESIDENT, 0, 0};
     if (wave_supported(c->precision, c->nx, c->ny, c->bc_x, c->bc_y) && c->nx >= 128 &&
-        c->ny >= 64)
-        for (int ks : {4, 5, 6})
-            for (int rows : {128, 256}) cands[nc++] = {KERNEL_WAVE, ks, rows};
+        c->ny >= 64) {
+        if (c->precision == PREC_FP32) {
+            for (int ks : {4, 5, 6})
+                for (int rows : {128, 256}) cands[nc++] = {KERNEL_WAVE, ks, rows};
+        } else {
+            for (int ks : {2, 3, 4})
+                for (int rows : {128, 256}) cands[nc++] = {KERNEL_WAVE, ks, rows};
+        }
+    }
 
     // keep the state: copy both buffers aside when the lattice holds one
     void *saved = nullptr;
@@ -1202,8 +1216,8 @@ lbm_status lbm_autotune(lbm_ctx *c, int trial_steps, int *kernel, double *us_per
 
 lbm_status lbm_set_wave_config(lbm_ctx *c, int steps, int rows) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
-    if (steps < WAVE_MIN_STEPS || steps > WAVE_MAX_STEPS)
-        return fail(c, LBM_EINVAL, "steps per launch must be 2..8");
+    if (steps < WAVE_MIN_STEPS || steps > wave_max_steps(c->precision))
+        return fail(c, LBM_EINVAL, "steps per launch must be 2..8 (2..4 with 16-bit storage)");
     if (rows < 1) return fail(c, LBM_EINVAL, "rows per segment must be >= 1");
     if (steps != c->wave_steps || rows != c->wave_rows) {
         DeviceGuard g(c->device);

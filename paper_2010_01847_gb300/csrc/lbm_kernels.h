@@ -153,9 +153,17 @@ cudaError_t launch_resident(const float *src, float *out_last, float *out_prev, 
 // (wave_supported) or src == dst.
 constexpr int WAVE_MIN_STEPS = 2;
 constexpr int WAVE_MAX_STEPS = 8;
+constexpr int WAVE16_MAX_STEPS = 4;     // 16-bit storage (wave16.cu)
 bool wave_supported(int precision, int nx, int ny, int bc_x, int bc_y);
+int wave_max_steps(int precision);
 cudaError_t launch_step_wave(int steps, const float *src, float *dst, int nx, int ny, int bc_x,
                              int bc_y, const Coef<float> &k, int seg_rows, cudaStream_t stream);
+// The same for FP16 / BF16 storage with tile references (nx % 8 == 0): level
+// 0 decoded, levels in FP32, level `steps` stored against the reference of
+// level steps - 1 (rounded once per launch).
+cudaError_t launch_step_wave16(int precision, int steps, const void *src, void *dst, int nx,
+                               int ny, int bc_x, int bc_y, const Coef<float> &k, int seg_rows,
+                               cudaStream_t stream);
 // Runs the staged kernel's bounded mbarrier wait against a barrier nothing
 // completes (one CTA, ~2 s); the wait gives up and ORs 1 into *status.
 cudaError_t launch_wait_probe(int *status, cudaStream_t stream);

@@ -43,9 +43,16 @@ cudaError_t launch_k(const Strip &a, const Coef<float> &k, cudaStream_t stream) 
 
 bool wave_supported(int precision, int nx, int ny, int bc_x, int bc_y) {
     (void)ny;
-    return precision == PREC_FP32 && nx >= 2 && nx % 2 == 0 &&
-           (bc_x == BC_PERIODIC || bc_x == BC_GRADIENT) &&
-           (bc_y == BC_PERIODIC || bc_y == BC_WALLS);
+    const bool bc_ok = (bc_x == BC_PERIODIC || bc_x == BC_GRADIENT) &&
+                       (bc_y == BC_PERIODIC || bc_y == BC_WALLS);
+    if (precision == PREC_FP32) return bc_ok && nx >= 2 && nx % 2 == 0;
+    // 16-bit storage: tiles of 8 nodes (4 lanes of a strip)
+    if (has_tile_refs(precision)) return bc_ok && nx >= 8 && nx % 8 == 0;
+    return false;
+}
+
+int wave_max_steps(int precision) {
+    return precision == PREC_FP32 ? WAVE_MAX_STEPS : WAVE16_MAX_STEPS;
 }
 
 cudaError_t launch_step_wave(int steps, const float *src, float *dst, int nx, int ny, int bc_x,

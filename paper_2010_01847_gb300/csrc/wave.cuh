@@ -96,6 +96,38 @@ __device__ __forceinline__ void stage_row(float2 *ring, const Strip &a, int xa, 
     cp_commit();
 }
 
+// The pull of one row of a level from rows r - 1, r, r + 1 of the level
+// below (Eq. 13 left-hand side on the lane's node pair: c_y from the row
+// below or above, c_x from the lane's other node or the neighbouring lane),
+// the seam jump (Eqs. 59-60) and the walls (Eq. 58).  Every lane calls it.
+template <bool SEAM>
+__device__ __forceinline__ void pull_level(const float2 (&below)[8], const float2 (&here)[8],
+                                           const float2 (&above)[8], const Coef<float> &k,
+                                           bool seam_a, bool seam_b, bool walls, int r, int ny,
+                                           float2 (&d)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i);
+        const float2 v = cy > 0 ? below[i] : (cy < 0 ? above[i] : here[i]);
+        const float jw = i < 4 ? k.jump_axis : k.jump_diag;
+        if (cx > 0) {        // node a from the left lane's node b, node b from node a
+            float left = __shfl_up_sync(0xffffffffu, v.y, 1);
+            if (SEAM && seam_a) left = left + jw;            // Eq. 59
+            d[i] = make_float2(left, v.x);
+        } else if (cx < 0) { // node b from the right lane's node a, node a from node b
+            float right = __shfl_down_sync(0xffffffffu, v.x, 1);
+            if (SEAM && seam_b) right = right - jw;          // Eq. 60
+            d[i] = make_float2(v.y, right);
+        } else {
+            d[i] = v;
+        }
+    }
+    if (walls) {
+        if (r == 0) wall_bottom(d, k);
+        if (r == ny - 1) wall_top(d, k);
+    }
+}
+
 // One march position s with s - s_lo = P (mod 3).  SEAM: some lane of the
 // warp pulls across the seam of a gradient lattice (else no jump is added).
 template <int K, int P, bool SEAM>
@@ -125,27 +157,7 @@ __device__ __forceinline__ void march_step(March<K> &m, const Strip &a, const Co
         const float2(&here)[8] = m.w[l - 1][mod3(P - l)];        // row r
         const float2(&above)[8] = m.w[l - 1][mod3(P - l + 1)];   // row r + 1
         float2 d[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int cx = cx_of(i), cy = cy_of(i);
-            const float2 v = cy > 0 ? below[i] : (cy < 0 ? above[i] : here[i]);
-            const float jw = i < 4 ? k.jump_axis : k.jump_diag;
-            if (cx > 0) {        // node a from the left lane's node b, node b from node a
-                float left = __shfl_up_sync(0xffffffffu, v.y, 1);
-                if (SEAM && seam_a) left = left + jw;            // Eq. 59
-                d[i] = make_float2(left, v.x);
-            } else if (cx < 0) { // node b from the right lane's node a, node a from node b
-                float right = __shfl_down_sync(0xffffffffu, v.x, 1);
-                if (SEAM && seam_b) right = right - jw;          // Eq. 60
-                d[i] = make_float2(v.y, right);
-            } else {
-                d[i] = v;
-            }
-        }
-        if (walls) {
-            if (r == 0) wall_bottom(d, k);
-            if (r == a.ny - 1) wall_top(d, k);
-        }
+        pull_level<SEAM>(below, here, above, k, seam_a, seam_b, walls, r, a.ny, d);
         collide_f32<float2>(d, k);
         if (l < K) {
 #pragma unroll

@@ -58,8 +58,9 @@ def _kernel_ok(kernel, nx, precision):
         return precision in ("fp32", "fp64") and nx % (256 * v) == 0
     if kernel == "resident":
         return precision == "fp32"          # every lattice here fits one cluster
-    if kernel == "wave":                    # FP32 storage, node pairs along x
-        return precision == "fp32" and nx % 2 == 0
+    if kernel == "wave":                    # node pairs along x; 16-bit: whole tiles of 8
+        return nx % 2 == 0 if precision == "fp32" else (
+            precision in ("fp16", "bf16") and nx % 8 == 0)
     return True
 
 

@@ -9,7 +9,7 @@ import pytest
 
 import paper_2010_01847_gb300 as plbm
 from paper_2010_01847_gb300 import inputs
-from tests.helpers import tau_pair
+from tests.helpers import check_gate, err_metrics, oracle_run, tau_pair
 
 pytestmark = pytest.mark.gpu
 
@@ -125,10 +125,58 @@ def test_launch_timing_counts():
     assert g.launch_time(plbm.TIMED_WAVE) == (0.0, 0, 0)
 
 
+# 16-bit storage: levels in FP32 between launches, so a launch is not the
+# bits of single 16-bit steps; checked against the oracle (the 16-bit gate)
+CASES16 = [(256, 64, GRAD, WALLS), (128, 50, PER, PER), (64, 9, GRAD, WALLS),
+           (8, 5, GRAD, PER), (120, 6, GRAD, WALLS), (16, 2, GRAD, WALLS)]
+
+
+@pytest.mark.parametrize("precision,rounding", [("fp16", "nearest"), ("fp16", "stochastic"),
+                                                ("bf16", "nearest"), ("bf16", "stochastic")])
+@pytest.mark.parametrize("case", CASES16, ids=lambda c: f"{c[0]}x{c[1]}_bc{c[2]}{c[3]}")
+def test_16bit_multi_step_against_oracle(case, precision, rounding):
+    nx, ny, bx, by = case
+    f = fields(nx, ny)
+    steps = 37
+    o = oracle_run(nx, ny, 0.9, 12.0, f, steps, bx, by, 1e-3)
+    ref = o.moments()
+
+    def run(prec, kernel, K=4, rows=64):
+        g = lattice(nx, ny, bx, by, kernel, precision=prec, rounding=rounding)
+        if kernel == "wave":
+            g.set_wave_config(K, rows)
+        g.init(*f)
+        g.step(steps)
+        m = g.moments()
+        g.close()
+        return m
+
+    single = max(err_metrics(run(precision, "vector"), ref))
+    worst = None
+    for K, rows in ((2, 7), (3, 64), (4, 1), (4, 64)):
+        m = run(precision, "wave", K, rows)
+        assert np.array_equal(m[0], run(precision, "wave", K, rows)[0])     # deterministic
+        err = err_metrics(m, ref)
+        # one rounding per launch instead of per step: no worse than single steps
+        assert max(err) <= 1.5 * single + 1e-6, (K, rows, err, single)
+        if worst is None or max(err) > max(worst[0]):
+            worst = (err, K, rows)
+    (err_e, err_q), K, rows = worst
+    check_gate(precision, err_e, err_q,
+               fp16=lambda: err_metrics(run("fp16", "wave", K, rows), ref))
+
+
 def test_refusals():
     with pytest.raises(plbm.LBMError) as ex:
-        plbm.Lattice(256, 16, 0.9, 12.0, GRAD, WALLS, 1e-3, precision="fp16", kernel="wave")
+        plbm.Lattice(252, 16, 0.9, 12.0, GRAD, WALLS, 1e-3, precision="fp16", kernel="wave")
+    assert ex.value.status == plbm.EUNSUPPORTED          # 16-bit: nx a multiple of 8
+    with pytest.raises(plbm.LBMError) as ex:
+        plbm.Lattice(256, 16, 0.9, 12.0, GRAD, WALLS, 1e-3, precision="fp64", kernel="wave")
     assert ex.value.status == plbm.EUNSUPPORTED
+    h = plbm.Lattice(256, 16, 0.9, 12.0, GRAD, WALLS, 1e-3, precision="bf16", kernel="wave")
+    with pytest.raises(plbm.LBMError) as ex:
+        h.set_wave_config(5, 64)                          # 16-bit: up to 4 steps
+    assert ex.value.status == plbm.EINVAL
     with pytest.raises(plbm.LBMError) as ex:
         plbm.Lattice(255, 16, 0.9, 12.0, GRAD, WALLS, 1e-3, kernel="wave")      # nx odd
     assert ex.value.status == plbm.EUNSUPPORTED
