@@ -268,6 +268,7 @@ KERNEL_SOURCES = {
     "step_staged": ["lbm_device.cuh", "mbarrier.cuh", "staged.cu"],
     "step_scalar": ["lbm_device.cuh", "refs16.cuh", "stream_collide.cu"],
     "step_wave": ["lbm_device.cuh", "wave.cuh", "wave.cu"],
+    "step_wave16": ["lbm_device.cuh", "refs16.cuh", "wave.cuh", "wave16.cu"],
 }
 
 
@@ -442,7 +443,7 @@ def run_native(args):
     achieved = bps * sites / avg_launch / 1e9
     peak, peak_kind = measured_peak()
     if dom == plbm.TIMED_WAVE:
-        kname = "step_wave"
+        kname = "step_wave16" if STORAGE_BYTES[args.precision] == 2 else "step_wave"
     elif dom == plbm.TIMED_RESIDUAL:
         kname = "step_vector_residual"
     else:

@@ -124,8 +124,8 @@ typedef enum {
 typedef enum {
     LBM_KERNEL_AUTO = 0,     /* up to 16384 nodes: resident for LBM_FP32,     */
                              /* scalar for LBM_FP64; from 2^24 nodes (nx >=   */
-                             /* 256) wave for LBM_FP32 where it applies (4    */
-                             /* steps per launch, 256-row segments); else     */
+                             /* 256) wave where it applies (4 steps per       */
+                             /* launch, 256-row segments); else               */
                              /* vector when nx allows, else scalar            */
                              /* (lbm_autotune times the candidates)           */
     LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx                   */
@@ -148,14 +148,18 @@ typedef enum {
                              /* each warp advances a 64-column strip of a     */
                              /* segment of rows K levels in registers         */
                              /* (lbm_set_wave_config), reading and writing    */
-                             /* the planes once per K steps; same results bit */
-                             /* for bit.  LBM_FP32 storage, nx even, x        */
-                             /* periodic (with or without the gradient), y    */
-                             /* periodic or walled; else LBM_EUNSUPPORTED.    */
-                             /* lbm_step(n) ends with one single step (vector */
-                             /* kernel, else scalar), which the read-outs     */
-                             /* need; lbm_step_residual(n) runs n - 1 steps   */
-                             /* in multi-step launches and its residual step  */
+                             /* the planes once per K steps.  LBM_FP32: nx    */
+                             /* even, same results bit for bit.  LBM_FP16_DEV */
+                             /* / LBM_BF16_DEV: nx % 8 == 0, K <= 4; levels   */
+                             /* in FP32, stored (rounded to 16 bits) once per */
+                             /* launch, so not the bits of single 16-bit      */
+                             /* steps.  x periodic (with or without the       */
+                             /* gradient), y periodic or walled; else         */
+                             /* LBM_EUNSUPPORTED.  lbm_step(n) ends with one  */
+                             /* single step (vector kernel, else scalar),     */
+                             /* which the read-outs need; lbm_step_residual(n)*/
+                             /* runs n - 1 steps in multi-step launches and   */
+                             /* its residual step                             */
 } lbm_kernel;
 
 typedef struct {
@@ -327,8 +331,9 @@ lbm_status lbm_get_staged_config(const lbm_ctx *ctx, int *stages, int *ctas_per_
 /* Autotuner: times every stream-collide kernel and staged shape that can
  * run this lattice (vector or scalar; staged with 2 or 3 stages and 8 or 4
  * consumer warps; cluster-resident; the multi-step kernel with 4, 5 or 6
- * steps per launch and segments of 128 or 256 rows, on lattices of at least
- * 128 x 64 nodes), trial_steps steps each (0 = 20) after 2 warm-up steps,
+ * steps per launch (2, 3 or 4 with 16-bit storage) and segments of 128 or
+ * 256 rows, on lattices of at least 128 x 64 nodes), trial_steps steps each
+ * (0 = 20) after 2 warm-up steps,
  * on the context's stream, and keeps the fastest for later lbm_step calls.
  * The timings run on the context's own buffers; when the context holds a
  * state (after lbm_init) both buffers are first copied to a temporary
@@ -344,7 +349,8 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int trial_steps, int *kernel, double *us_p
 lbm_status lbm_set_graph_chunk(lbm_ctx *ctx, int steps);
 
 /* Shape of the multi-step kernel (LBM_KERNEL_WAVE): `steps` time steps per
- * launch (2..8) and strips of `rows` rows (>= 1; clipped to ny).  A launch
+ * launch (2..8; 2..4 with 16-bit storage) and strips of `rows` rows (>= 1;
+ * clipped to ny).  A launch
  * reads and writes the planes once: 64 B per node per `steps` steps, plus
  * the 2 x steps rows of overlap each segment reads.  Each warp keeps about
  * 27 registers per step level (steps = 4: 158 per thread).  Defaults 4 and

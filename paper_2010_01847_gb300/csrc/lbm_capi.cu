@@ -395,10 +395,11 @@ int resolve_kernel(lbm_ctx *c, int requested) {
         else (void)cudaGetLastError();
     }
     if (requested == KERNEL_AUTO) {
-        // without timing (lbm_autotune times them): large FP32 lattices the
-        // multi-step kernel (4 steps per launch, 256-row segments: 320
-        // against 106 GLUPS at 8192^2; from 16 M nodes its strip-segments
-        // fill the GPU), else the vector kernel, the fastest single-step
+        // without timing (lbm_autotune times them): large lattices the
+        // multi-step kernel where it applies (4 steps per launch, 256-row
+        // segments: FP32 320 against 106, FP16 230 against 177 GLUPS at
+        // 8192^2; from 16 M nodes its strip-segments fill the GPU), else
+        // the vector kernel, the fastest single-step
         // kernel measured at 8192^2 for every storage kind (FP32 6.7, 16-bit
         // 6.5 TB/s against the staged kernel's 5.7 and 6.0), with the least
         // set-up for small, launch-latency bound lattices
