@@ -266,30 +266,39 @@ step_vector16_res(const T *__restrict__ src, T *__restrict__ dst, int nx, int ny
         const SeamAdd seam{need_left, x0 == 0 && grad, need_right, x0 + V == nx && grad};
         const long long out = (long long)y * nx + x0;
         const bool have_prev = rq.have_prev != 0;
-        auto residual = [&](int m, const float2 (&f)[8]) {
-            float2 h[3];
+        // the thread's 8 nodes of each history plane, read and written as
+        // 16-byte vectors around the collision (reading and writing them a
+        // pair at a time in between, each store invalidated the L1 line the
+        // next pair's load needed: 3x the step's time)
+        float h[3][8];
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
-                h[q] = have_prev
-                           ? *reinterpret_cast<const float2 *>(rq.prev + q * plane + out + 2 * m)
-                           : make_float2(0.f, 0.f);
+        for (int q = 0; q < 3; ++q) {
+            if (have_prev) {
+                load_cvec<float, 8>(rq.prev + q * plane + out, h[q]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) h[q][j] = 0.f;
+            }
+        }
+        auto residual = [&](int m, const float2 (&f)[8]) {
             float n0[8], n1[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 n0[i] = f[i].x;
                 n1[i] = f[i].y;
             }
-            residual_terms(n0, k, rq.inv_scale, h[0].x, h[1].x, h[2].x, have_prev, loc);
-            residual_terms(n1, k, rq.inv_scale, h[0].y, h[1].y, h[2].y, have_prev, loc);
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                *reinterpret_cast<float2 *>(rq.prev + q * plane + out + 2 * m) = h[q];
+            residual_terms(n0, k, rq.inv_scale, h[0][2 * m], h[1][2 * m], h[2][2 * m], have_prev,
+                           loc);
+            residual_terms(n1, k, rq.inv_scale, h[0][2 * m + 1], h[1][2 * m + 1],
+                           h[2][2 * m + 1], have_prev, loc);
         };
         float sums[3];
         float Re[8];
         ref_pops(ref_of<T>(enc), k, Re);
         collide_words16<T, SR>(w, k, seam, bottom, top, Rd, Rx, Re, sums, (unsigned)(out >> 1),
                                residual);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) store_cvec<float, 8>(rq.prev + q * plane + out, h[q]);
 #pragma unroll
         for (int i = 0; i < 8; ++i) st_stream(dst + (long long)i * plane + out, w[i]);
         st_ref(dst, k, t, enc, next_ref<T>(sums[0], sums[1], sums[2], k, k.ref_gamma));
