@@ -17,8 +17,9 @@
 // Tiles are the 8 nodes of a row from x = 8t; a lane's node pair (xa, xa + 1)
 // lies in one tile and 4 consecutive lanes hold a tile, the lane o
 // positions into it; strips have a halo of 4 columns whatever K (<= 4), so
-// that the 56 columns a strip writes are 7 whole tiles.  Tile sums use the tree ((0 + 2) + (4 + 6)) +
-// ((1 + 3) + (5 + 7)) of the single-step kernels.  Requires nx % 8 == 0.
+// that the 56 columns a strip writes are 7 whole tiles.  Tile sums use the
+// tree ((0 + 2) + (4 + 6)) + ((1 + 3) + (5 + 7)) of the single-step
+// kernels.  Requires nx % 8 == 0.
 #include "lbm_kernels.h"
 #include "refs16.cuh"
 #include "wave.cuh"
@@ -26,7 +27,6 @@
 namespace plbm {
 namespace {
 
-using wave::Strip;
 using wave::mod3;
 
 constexpr int W16_WARPS = 4;
@@ -112,7 +112,7 @@ __device__ __forceinline__ uint2 tile_next_ref(float2 rho, float2 mx, float2 my,
 
 template <int K>
 struct March16 {
-    float2 w[K][3][8];      // windows of levels 1..K-1 (w[0]: level 0, decoded)
+    float2 w[K][3][8];      // windows of levels 0..K-1 (level 0: decoded source rows)
     uint2 enc;              // reference of the row level K stores next
     unsigned *ring;
 };
