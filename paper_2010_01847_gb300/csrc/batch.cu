@@ -141,7 +141,7 @@ batch_kernel(const T *__restrict__ src, T *__restrict__ dst,
 // of the running instances (wave.cuh), with the instance's coefficients, a
 // common halo H and rows per segment.  Persistent grid: the item count is
 // read from device memory, so captured launches follow retirements.
-constexpr int BW_WARPS = 4;
+constexpr int BW_WARPS = 1;        // one strip-segment per block, as the single-lattice kernel
 constexpr int BW_SMEM = BW_WARPS * wave::RING_ELEMS * (int)sizeof(float2);
 
 template <int K>

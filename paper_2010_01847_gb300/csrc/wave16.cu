@@ -29,7 +29,7 @@ namespace {
 
 using wave::mod3;
 
-constexpr int W16_WARPS = 4;
+constexpr int W16_WARPS = 1;          // one strip per block, as the FP32 kernel
 constexpr int W16_RING = 4;
 // one ring slot: 8 planes x 32 lanes of one 32-bit word (the lane's node
 // pair), then 32 lanes x 8 bytes of stored-against reference
@@ -242,11 +242,11 @@ __device__ __forceinline__ void run_strip16(const Strip16 &a, const Coef<float> 
     wave::cp_wait<0>();
 }
 
-// 3 blocks of 4 warps per SM: the 4-step march fits 168 registers with a
-// few bytes of spills (219 -> 230 GLUPS for FP16 at 8192^2); fewer steps
-// fit without.
+// 12 warps per SM: the 4-step march fits 168 registers with a few bytes of
+// spills (219 -> 230 GLUPS for FP16 at 8192^2 with blocks of 4 warps);
+// fewer steps fit without.
 template <typename T, int K, bool SEAM, bool SR>
-__global__ void __launch_bounds__(W16_WARPS * 32, 3)
+__global__ void __launch_bounds__(W16_WARPS * 32, 12 / W16_WARPS)
 step_wave16(const Strip16 a, const Coef<float> k, int tiles_x, long long items) {
     extern __shared__ unsigned w16_ring[];
     const long long item = (long long)blockIdx.x * W16_WARPS + (threadIdx.x >> 5);
