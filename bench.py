@@ -776,7 +776,8 @@ def steady_state_study(n_train, train_steps, n_test, n_ref, tol, check_every, ma
     periodic gradient from three starts, and their accuracy.
 
     Training: n_train channels' steady states from the batched solver (on
-    channels shortened to 8 columns, whose steady rows are the full ones'),
+    channels shortened to 8 columns, whose steady rows are the full ones';
+    solved from the analytic start),
     the network trained on the GPU (train_steps Adam steps, minibatches of
     512).  Held-out: n_test channels of length 4W from a seed training never
     saw, solved from the cold start (e = e_ref, q = 0), the analytic start
@@ -788,8 +789,9 @@ def steady_state_study(n_train, train_steps, n_test, n_ref, tol, check_every, ma
     t0 = time.perf_counter()
     train = warmstart.channels(n_train, seed=inputs.SEED + 1, nx=warmstart.TRAIN_NX,
                                w_range=w_range)
+    # the training steady states, solved from the analytic start (Eq. 68)
     prof, tsteps, tr, t_gen = warmstart.steady_profiles(train, tol, check_every, max_steps,
-                                                        schedule="tune")
+                                                        schedule="tune", start="analytic")
     ws = warmstart.WarmStart(seed=0, max_batch=max(512, n_train))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
