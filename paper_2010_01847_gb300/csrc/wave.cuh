@@ -22,16 +22,18 @@
 // A strip's outer columns depend on columns outside it: after l levels the
 // l outermost columns on each side are wrong, so the strip overlaps its
 // neighbours by a halo of H >= K columns each side (even, so that pairs stay
-// 8-byte aligned) and writes only its 64 - 2H middle columns.  Likewise a segment of rows [y0, y1) starts its
-// march K rows early and ends K rows late (periodic y), or at the walls,
-// where no rows lie beyond (the wall rule of Eq. 58 replaces every
-// population that would come from beyond them).
+// 8-byte aligned) and writes only its 64 - 2H middle columns.  Likewise a
+// segment of rows [y0, y1) starts its march K rows early and ends K rows
+// late (periodic y), or at the walls, where no rows lie beyond (the wall
+// rule of Eq. 58 replaces every population that would come from beyond
+// them).
 //
 // Bytes per site update: one read and one write of the 8 planes per K steps,
 // (32 + 32) / K B plus the halo rows re-read by adjacent segments (2K / rows
 // of the reads); the halo columns are read by two strips at nearly the same
-// time and come from L2.  Requires FP32 storage, nx even, x periodic (with
-// or without the seam gradient) and y periodic or walled; no sides.
+// time and come from L2.  The FP32 march requires nx even, x periodic (with
+// or without the seam gradient) and y periodic or walled; no sides.  The
+// 16-bit march (wave16.cu) reuses pull_level and the ring helpers.
 #pragma once
 
 #include "lbm_device.cuh"
