@@ -387,6 +387,7 @@ Coef<C> coef_of(const lbm_instance &in, double scale, int precision) {
     k.omega = (C)(1.0 / p.tau);
     k.sigma = (C)p.sigma;
     k.lambda = (C)p.lambda;
+    k.zeta = (C)(p.lambda + p.sigma * p.tau * (1.0 - p.lambda));
     k.w_axis = (C)(2.0 / 9.0);
     k.w_diag = (C)0.25 - k.w_axis;
     k.h_axis = (C)(1.0 / 3.0);

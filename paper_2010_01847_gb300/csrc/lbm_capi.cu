@@ -127,7 +127,9 @@ Coef<C> make_coef(const lbm_ctx *c) {
     Coef<C> k{};
     k.omega = (C)(1.0 / c->tau);
     k.sigma = (C)c->sigma;
-    k.lambda = (C)(std::isinf(c->tau_r) ? 0.0 : 1.0 / (2.0 * c->tau_r + 1.0));
+    const double lambda = std::isinf(c->tau_r) ? 0.0 : 1.0 / (2.0 * c->tau_r + 1.0);
+    k.lambda = (C)lambda;
+    k.zeta = (C)(lambda + c->sigma * c->tau * (1.0 - lambda));
     k.w_axis = (C)(2.0 / 9.0);
     k.w_diag = (C)0.25 - k.w_axis;                  // exact: 4 w_axis + 4 w_diag = 1
     k.h_axis = (C)(1.0 / 3.0);

@@ -29,7 +29,12 @@ enum { SIDE_DIFFUSE = 0, SIDE_ISOTHERMAL = 1, SIDE_HEAT_FLUX = 2 };
 //   eq_i = w_i rho + t_i                     (Eq. 15 on deviations),
 // the post-collision deviation is (Eq. 13 right-hand side with Eq. 16)
 //   d_i* = d_i - omega (d_i - eq_i) - sigma t_i,
-// omega = 1/tau, sigma = (1 - 1/(2 tau)) / tau_r.
+// omega = 1/tau, sigma = (1 - 1/(2 tau)) / tau_r.  The FP32 collision
+// (relax_f32) takes the same update with the resistive term inside the
+// relaxation, d_i* = d_i - omega (d_i - w_i rho - t'_i), where t'_i is t_i
+// with (1 - zeta) m in place of q, zeta = lambda + sigma tau (1 - lambda), so
+// that omega (1 - zeta) = omega (1 - lambda) - sigma (1 - lambda): one
+// rounded coefficient for the flux factor instead of two terms.
 // The rounded coefficients keep the sums the scheme conserves exact in the
 // rounded values: 4 w_axis + 4 w_diag = 1, 2 h_axis + 4 h_diag = 1 and
 // u_axis + 2 u_diag = 1 hold exactly (w_diag = 1/4 - w_axis and the other
@@ -40,6 +45,7 @@ enum { SIDE_DIFFUSE = 0, SIDE_ISOTHERMAL = 1, SIDE_HEAT_FLUX = 2 };
 template <typename C>
 struct Coef {
     C omega, sigma, lambda;
+    C zeta;                   // lambda + sigma tau (1 - lambda), the FP32 flux factor's complement
     C w_axis, w_diag;         // Eq. 17
     C h_axis, h_diag;         // (5/3) a_i, Eq. 18
     C u_axis, u_diag;         // Eq. 58: w_i / (5/18) = 4/5 and 1/10
@@ -130,19 +136,21 @@ template <typename V> __device__ __forceinline__ V splat(float c);
 template <> __device__ __forceinline__ float splat<float>(float c) { return c; }
 template <> __device__ __forceinline__ float2 splat<float2>(float c) { return make_float2(c, c); }
 
-// One population's relaxation, d* = d - omega (d - eq) - sigma t_i, with
-// eq = w rho + t_i formed in one rounding (fused multiply-add) and t_i = +t
-// (plus) or -t (minus).  For minus the negated equilibrium -eq = w (-rho) + t
-// is formed instead (rounding is symmetric, so it is exactly -eq) and added.
+// One population's relaxation, d* = d - omega (d - eq), with eq = w rho + t_i
+// formed in one rounding (fused multiply-add) and t_i = +t (plus) or -t
+// (minus); t carries the flux factor 1 - zeta, which holds the resistive
+// term sigma t_i of Eq. 16.  For minus the negated equilibrium
+// -eq = w (-rho) + t is formed instead (rounding is symmetric, so it is
+// exactly -eq) and added.
 template <typename V>
-__device__ __forceinline__ V relax_plus(V d, V w, V rho, V t, V neg_omega, V neg_sigma) {
+__device__ __forceinline__ V relax_plus(V d, V w, V rho, V t, V neg_omega) {
     const V eq = f_fma(w, rho, t);
-    return f_fma(neg_sigma, t, f_fma(neg_omega, f_sub(d, eq), d));
+    return f_fma(neg_omega, f_sub(d, eq), d);
 }
 template <typename V>
-__device__ __forceinline__ V relax_minus(V d, V w, V neg_rho, V t, V neg_omega, V sigma) {
+__device__ __forceinline__ V relax_minus(V d, V w, V neg_rho, V t, V neg_omega) {
     const V neg_eq = f_fma(w, neg_rho, t);
-    return f_fma(sigma, t, f_fma(neg_omega, f_add(d, neg_eq), d));
+    return f_fma(neg_omega, f_add(d, neg_eq), d);
 }
 
 // The moments of Eqs. 53-54 before the kappa factor: rho = sum d_i and
@@ -159,9 +167,9 @@ __device__ __forceinline__ void moments_f32(const V (&d)[8], V &rho, V &mx, V &m
 // The relaxation of collide_f32 given the node's moments.
 template <typename V>
 __device__ __forceinline__ void relax_f32(V (&d)[8], V rho, V mx, V my, const Coef<float> &k) {
-    const V neg_lambda = splat<V>(-k.lambda);
-    const V qx = f_fma(neg_lambda, mx, mx);             // q = m - lambda m
-    const V qy = f_fma(neg_lambda, my, my);
+    const V neg_zeta = splat<V>(-k.zeta);
+    const V qx = f_fma(neg_zeta, mx, mx);               // (1 - zeta) m
+    const V qy = f_fma(neg_zeta, my, my);
     const V neg_rho = f_mul(splat<V>(-1.f), rho);       // exact
     const V wa = splat<V>(k.w_axis), wd = splat<V>(k.w_diag);
     const V ha = splat<V>(k.h_axis), hd = splat<V>(k.h_diag);
@@ -169,16 +177,16 @@ __device__ __forceinline__ void relax_f32(V (&d)[8], V rho, V mx, V my, const Co
     const V tb = f_mul(ha, qy);
     const V tp = f_mul(hd, f_add(qx, qy));
     const V tm = f_mul(hd, f_sub(qx, qy));
-    const V no = splat<V>(-k.omega), ns = splat<V>(-k.sigma), sg = splat<V>(k.sigma);
+    const V no = splat<V>(-k.omega);
     // t_i for i = 0..7: ta, tb, -ta, -tb, tp, -tm, -tp, tm
-    d[0] = relax_plus(d[0], wa, rho, ta, no, ns);
-    d[1] = relax_plus(d[1], wa, rho, tb, no, ns);
-    d[2] = relax_minus(d[2], wa, neg_rho, ta, no, sg);
-    d[3] = relax_minus(d[3], wa, neg_rho, tb, no, sg);
-    d[4] = relax_plus(d[4], wd, rho, tp, no, ns);
-    d[5] = relax_minus(d[5], wd, neg_rho, tm, no, sg);
-    d[6] = relax_minus(d[6], wd, neg_rho, tp, no, sg);
-    d[7] = relax_plus(d[7], wd, rho, tm, no, ns);
+    d[0] = relax_plus(d[0], wa, rho, ta, no);
+    d[1] = relax_plus(d[1], wa, rho, tb, no);
+    d[2] = relax_minus(d[2], wa, neg_rho, ta, no);
+    d[3] = relax_minus(d[3], wa, neg_rho, tb, no);
+    d[4] = relax_plus(d[4], wd, rho, tp, no);
+    d[5] = relax_minus(d[5], wd, neg_rho, tm, no);
+    d[6] = relax_minus(d[6], wd, neg_rho, tp, no);
+    d[7] = relax_plus(d[7], wd, rho, tm, no);
 }
 
 // The collision above in FP32 on one node (V = float) or on two nodes at once

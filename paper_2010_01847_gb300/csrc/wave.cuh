@@ -83,14 +83,25 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// Row position s wrapped into [0, ny): one compare in the march's middle, a
+// subtraction or addition of ny within K rows of its ends, and the remainder
+// only for lattices fewer rows high than the march runs past them (s is the
+// same in every lane).
+__device__ __forceinline__ int wrap_row(int s, int ny) {
+    if (s >= 0 && s < ny) return s;
+    if (s >= ny && s < 2 * ny) return s - ny;
+    if (s < 0 && s >= -ny) return s + ny;
+    const int r = s % ny;
+    return r < 0 ? r + ny : r;
+}
+
 // Issues the copies of source row position s (wrapped into [0, ny)) into
 // its ring slot, as one commit group (an empty group past the last row, so
 // the group count per position stays one).
 __device__ __forceinline__ void stage_row(float2 *ring, const Strip &a, int xa, int s, int slot,
                                           bool load) {
     if (load) {
-        int r = s % a.ny;
-        if (r < 0) r += a.ny;
+        const int r = wrap_row(s, a.ny);
         const float *p = a.src + (long long)r * a.nx + xa;
 #pragma unroll
         for (int i = 0; i < 8; ++i) cp_async8(ring + (slot * 8 + i) * 32, p + (long long)i * a.plane);

@@ -67,8 +67,7 @@ __device__ __forceinline__ void stage_row16(unsigned *ring, int lane, const Stri
                                             const Coef<float> &k, int xa, int s, int slot,
                                             bool load) {
     if (load) {
-        int r = s % a.ny;
-        if (r < 0) r += a.ny;
+        const int r = wave::wrap_row(s, a.ny);
         const T *base = (const T *)a.src;
         const T *p = base + (long long)r * a.nx + xa;
         unsigned *sl = ring + slot * W16_SLOT_WORDS;

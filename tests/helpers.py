@@ -20,9 +20,15 @@ TOL = {"fp32": 1e-5, "fp16": 2e-3, "bf16": 2e-3, "fp64": 1e-8}
 # rounding per stored population and step (the arithmetic is FP32 in both),
 # so on the same case the BF16 error is about 8 times the FP16 one.  A BF16
 # result that misses the gate is an expected failure only within that
-# derived floor (8 times the FP16 error of the same case, times 1.5 for the
+# derived floor (8 times the FP16 error of the same case, times 2 for the
 # spread of rounding); beyond it, or without the FP16 comparison, it fails.
-BF16_OVER_FP16 = 8.0 * 1.5
+# The spread: the maximum error of one case is one realisation of the
+# roundings, and on small lattices a few roundings decide it.  On the 8 x 2
+# walled lattice (16 nodes, 57 steps) a change of the FP32 collision by about
+# one ulp per step moved the FP16 maximum error by a factor 1.85 (8.8e-4 to
+# 4.8e-4) while every BF16 rounding stayed the same (a BF16 rounding
+# boundary is 8 times further away in relative terms).
+BF16_OVER_FP16 = 8.0 * 2.0
 
 
 def err_metrics(gpu, orc):

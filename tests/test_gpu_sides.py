@@ -157,7 +157,13 @@ def test_sides_vector_equals_scalar_bitwise():
     assert np.array_equal(fa, fb)
     for x, y in zip(ma, mb):
         assert np.array_equal(x, y)
-    assert ea == pytest.approx(eb, rel=1e-12) and rb == pytest.approx(ra, rel=1e-6)
+    # the residual step sums each node's terms over a warp in FP32, then in
+    # FP64: the scalar kernel groups 32 single nodes, the vector kernel 32
+    # vectors of 4, so the energies agree to the FP32 rounding of warp sums
+    # of at most 128 terms, (128 - 1) 2^-24 sum |e - e_ref| (e_ref = 1)
+    bound = 127 * 2.0 ** -24 * float(np.abs(ma[0] - 1.0).sum())
+    assert abs(ea - eb) <= bound, (ea, eb, bound)
+    assert rb == pytest.approx(ra, rel=1e-6)
 
 
 def test_sides_kernel_choice_and_errors():
