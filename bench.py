@@ -260,6 +260,12 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# FP32 operations of the collision per node and step in the kernels that
+# compute in FP32 (FP32 and 16-bit storage): 15 for the moments, 9 for the
+# flux terms, 3 per population
+FP32_OPS_PER_UPDATE = {"fp32": 48, "fp16": 48, "bf16": 48}
+NOMINAL_SM_MHZ = 2070.0
+
 # sources that define each stream-collide kernel
 KERNEL_SOURCES = {
     "step_vector": ["lbm_device.cuh", "vector_pull.cuh", "stream_collide.cu"],
@@ -281,19 +287,22 @@ def kernel_source_hash(kernel_name):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_name, precision, nx, ny):
+def ncu_traffic(kernel_name, precision, nx, ny, shape=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current sources of that kernel (else None), scaled by sites."""
+    on the current sources of that kernel (else None), scaled by sites.  A
+    multi-step kernel's line names its shape (`step_wave:5x128`: steps per
+    launch x segment rows, which set the overlap rows it reads)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path) or kernel_name not in KERNEL_SOURCES:
         return None
     src = kernel_source_hash(kernel_name)
+    key = kernel_name if shape is None else f"{kernel_name}:{shape['steps']}x{shape['rows']}"
     for line in open(path):
         f = line.split()
         if len(f) < 7 or f[0].startswith("#"):
             continue
         kname, prec, snx, sny, nbytes, shash = f[0], f[1], int(f[2]), int(f[3]), float(f[4]), f[5]
-        if kname == kernel_name and prec == precision and shash == src:
+        if kname == key and prec == precision and shash == src:
             return nbytes * (nx * ny) / (snx * sny)   # traffic grows with the sites
     return None
 
@@ -442,8 +451,10 @@ def run_native(args):
     avg_launch = kern_ms / 1e3 / kern_launches
     achieved = bps * sites / avg_launch / 1e9
     peak, peak_kind = measured_peak()
+    shape = None
     if dom == plbm.TIMED_WAVE:
         kname = "step_wave16" if STORAGE_BYTES[args.precision] == 2 else "step_wave"
+        shape = lat.wave_config
     elif dom == plbm.TIMED_RESIDUAL:
         kname = "step_vector_residual"
     else:
@@ -451,7 +462,7 @@ def run_native(args):
         if kname == "step_vector" and STORAGE_BYTES[args.precision] == 2:
             kname = "step_pipe16"           # plain 16-bit steps: the pipelined node-pair kernel
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(kname, args.precision, nx, ny),
+            "frac": achieved / peak, "traffic": ncu_traffic(kname, args.precision, nx, ny, shape),
             "peak_source": f"{peak_kind} ({'MEASURED_PEAKS.json hbm_gbs' if peak_kind == 'measured' else 'profiling-recipe fallback 6.8 TB/s'})",
             "kernel": kname, "bytes_per_launch_site": bps,
             "steps_per_launch": kern_steps / kern_launches,
@@ -471,10 +482,16 @@ def run_native(args):
         out = [torch.empty((ny, nx), dtype=torch.float64).pin_memory() for _ in range(3)]
         hp = host.numpy()
         op = [o.numpy() for o in out]
-        # pinning ~2 GB above leaves the GPU idle for a while: warm it up
-        # again, untimed, as before the device-timed region
+        # pinning ~2 GB above leaves the GPU idle for a second or more: warm
+        # it up again, untimed, for the warm-up steps and at least 0.3 s of
+        # stepping (20 steps of the 8192^2 lattice take 4 ms, too short for
+        # the clocks to come back: the first e2e runs lost ~50 ms that way)
         chunked(max(args.warmup, 3))
         torch.cuda.synchronize()
+        t_warm = time.perf_counter()
+        while time.perf_counter() - t_warm < 0.3:
+            chunked(window)
+            torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t_start = time.perf_counter()
@@ -507,6 +524,20 @@ def run_native(args):
 
     if rank == 0:
         clocks = sampler.summary()
+        if FP32_OPS_PER_UPDATE.get(args.precision):
+            # the same launches against the FP32 pipe: the collision's
+            # operations per useful site update (an FMA counts one) over the
+            # launch time, against 128 FP32 lanes per SM at the sampled
+            # maximum SM clock; halo columns and overlap rows that the
+            # multi-step kernel computes twice are not counted
+            ops = FP32_OPS_PER_UPDATE[args.precision]
+            mhz = clocks.get("sm_max_mhz") or NOMINAL_SM_MHZ
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak_ops = sms * 128 * mhz * 1e6 / 1e12
+            got = ops * sites * roof["steps_per_launch"] / (roof["avg_launch_us"] * 1e-6) / 1e12
+            roof["fp32_pipe"] = {"bound": "alu", "ops_per_site_update": ops, "achieved": got,
+                                 "peak": peak_ops, "unit": "TOP/s", "frac": got / peak_ops,
+                                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:g} MHz"}
         line = {
             "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,

@@ -154,14 +154,17 @@ __device__ __forceinline__ V relax_minus(V d, V w, V neg_rho, V t, V neg_omega) 
 }
 
 // The moments of Eqs. 53-54 before the kappa factor: rho = sum d_i and
-// m = sum c_i d_i, in the order every FP32 kernel forms them.
+// m = sum c_i d_i, in the order every FP32 kernel forms them (15
+// operations: my subtracts d_7 - d_5, which rounds to exactly minus
+// d_5 - d_7, instead of adding the latter).
 template <typename V>
 __device__ __forceinline__ void moments_f32(const V (&d)[8], V &rho, V &mx, V &my) {
     rho = f_add(f_add(f_add(d[0], d[2]), f_add(d[1], d[3])),
                 f_add(f_add(d[4], d[6]), f_add(d[5], d[7])));
     const V s46 = f_sub(d[4], d[6]);
-    mx = f_add(f_add(f_sub(d[0], d[2]), s46), f_sub(d[7], d[5]));
-    my = f_add(f_add(f_sub(d[1], d[3]), s46), f_sub(d[5], d[7]));
+    const V s75 = f_sub(d[7], d[5]);
+    mx = f_add(f_add(f_sub(d[0], d[2]), s46), s75);
+    my = f_sub(f_add(f_sub(d[1], d[3]), s46), s75);
 }
 
 // The relaxation of collide_f32 given the node's moments.
@@ -191,9 +194,14 @@ __device__ __forceinline__ void relax_f32(V (&d)[8], V rho, V mx, V my, const Co
 
 // The collision above in FP32 on one node (V = float) or on two nodes at once
 // (V = float2: lane x one node, lane y the other).  Operation order chosen
-// for accuracy: over 5000 steps of the 4096 x 4 second-sound pulse
-// (Kn_R = 0.1) the max error against FP64 is 7e-6 with eq in one rounding,
-// 1.2e-5 with w rho rounded separately.
+// for accuracy and count (48 operations per node): over 5000 steps of the
+// 4096 x 4 second-sound pulse (Kn_R = 0.1) the max error against FP64 is
+// 6.2e-6 (7.1e-6 with sigma t_i as a separate term, 56 operations; 1.2e-5
+// with w rho also rounded apart from t_i), and 6.6e-8 against 8.1e-7 at
+// 300 steps of the 8192 x 8192 heat mode.  Folding omega into the weights
+// instead (d* = (1 - omega) d + omega eq, 41 operations) loses the small
+// differences d - eq: about 80 times less accurate at Kn_R = 1 and 10 on the
+// second-sound pulse (FP32 emulated on the host).
 template <typename V>
 __device__ __forceinline__ void collide_f32(V (&d)[8], const Coef<float> &k) {
     V rho, mx, my;
