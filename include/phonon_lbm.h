@@ -462,7 +462,7 @@ lbm_status lbm_batch_get_wave(const lbm_batch *batch, int *steps, int *rows);
 
 /* Autotuner: times every schedule above (trial_steps steps each, 0 = 10)
  * on the initialised batch and, with LBM_FP32 storage, multi-step launches
- * of 3 or 4 steps with segments of 64 or 128 rows; keeps the fastest per
+ * of 3, 4 or 5 steps with segments of 64 or 128 rows; keeps the fastest per
  * step (us_per_step).  The state is copied aside (2 x population bytes of
  * temporary device memory) and restored.  Synchronous. */
 lbm_status lbm_batch_autotune(lbm_batch *batch, int trial_steps, double *us_per_step);

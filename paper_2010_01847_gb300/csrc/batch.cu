@@ -1126,7 +1126,7 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, double *us_per_step
         b->tpi = best_t;
         b->ctas_per_sm = best_c;
         if (plan_grid(b) != cudaSuccess) (void)cudaGetLastError();
-        for (int ks : {3, 4}) {
+        for (int ks : {3, 4, 5}) {
             for (int rows : {64, 128}) {
                 b->wave_steps = ks;
                 b->wave_rows = rows;
