@@ -15,13 +15,13 @@ using wave::Strip;
 constexpr int WAVE_WARPS = 1;
 constexpr int WAVE_SMEM = WAVE_WARPS * wave::RING_ELEMS * (int)sizeof(float2);
 
-template <int K, bool SEAM>
+template <int K, bool SEAM, bool WALLS>
 __global__ void __launch_bounds__(WAVE_WARPS * 32)
 step_wave(const Strip a, const Coef<float> k, int tiles_x, long long items) {
     extern __shared__ float2 wave_ring[];
     const long long item = (long long)blockIdx.x * WAVE_WARPS + (threadIdx.x >> 5);
     if (item >= items) return;                   // whole warps leave together
-    wave::run_strip<K, SEAM>(a, k, int(item % tiles_x), int(item / tiles_x), wave::halo(K),
+    wave::run_strip<K, SEAM, WALLS>(a, k, int(item % tiles_x), int(item / tiles_x), wave::halo(K),
                              wave_ring + (threadIdx.x >> 5) * wave::RING_ELEMS);
 }
 
@@ -33,12 +33,16 @@ cudaError_t launch_k(const Strip &a, const Coef<float> &k, cudaStream_t stream) 
     const long long items = (long long)tiles_x * segs;
     const long long blocks = (items + WAVE_WARPS - 1) / WAVE_WARPS;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (a.bc_x == BC_GRADIENT)
-        step_wave<K, true><<<(unsigned)blocks, WAVE_WARPS * 32, WAVE_SMEM, stream>>>(a, k, tiles_x,
-                                                                                    items);
+    const unsigned g = (unsigned)blocks;
+    const bool seam = a.bc_x == BC_GRADIENT, walls = a.bc_y == BC_WALLS;
+    if (seam && walls)
+        step_wave<K, true, true><<<g, WAVE_WARPS * 32, WAVE_SMEM, stream>>>(a, k, tiles_x, items);
+    else if (seam)
+        step_wave<K, true, false><<<g, WAVE_WARPS * 32, WAVE_SMEM, stream>>>(a, k, tiles_x, items);
+    else if (walls)
+        step_wave<K, false, true><<<g, WAVE_WARPS * 32, WAVE_SMEM, stream>>>(a, k, tiles_x, items);
     else
-        step_wave<K, false><<<(unsigned)blocks, WAVE_WARPS * 32, WAVE_SMEM, stream>>>(a, k, tiles_x,
-                                                                                     items);
+        step_wave<K, false, false><<<g, WAVE_WARPS * 32, WAVE_SMEM, stream>>>(a, k, tiles_x, items);
     return cudaGetLastError();
 }
 

@@ -113,7 +113,8 @@ __device__ __forceinline__ void stage_row(float2 *ring, const Strip &a, int xa, 
 // below (Eq. 13 left-hand side on the lane's node pair: c_y from the row
 // below or above, c_x from the lane's other node or the neighbouring lane),
 // the seam jump (Eqs. 59-60) and the walls (Eq. 58).  Every lane calls it.
-template <bool SEAM>
+// WALLS = false: the lattice has no walls (the wall rule is not compiled).
+template <bool SEAM, bool WALLS = true>
 __device__ __forceinline__ void pull_level(const float2 (&below)[8], const float2 (&here)[8],
                                            const float2 (&above)[8], const Coef<float> &k,
                                            bool seam_a, bool seam_b, bool walls, int r, int ny,
@@ -135,7 +136,7 @@ __device__ __forceinline__ void pull_level(const float2 (&below)[8], const float
             d[i] = v;
         }
     }
-    if (walls) {
+    if (WALLS && walls) {
         if (r == 0) wall_bottom(d, k);
         if (r == ny - 1) wall_top(d, k);
     }
@@ -143,7 +144,7 @@ __device__ __forceinline__ void pull_level(const float2 (&below)[8], const float
 
 // One march position s with s - s_lo = P (mod 3).  SEAM: some lane of the
 // warp pulls across the seam of a gradient lattice (else no jump is added).
-template <int K, int P, bool SEAM>
+template <int K, int P, bool SEAM, bool WALLS>
 __device__ __forceinline__ void march_step(March<K> &m, const Strip &a, const Coef<float> &k,
                                            int s, int xa, bool out_lane, bool seam_a,
                                            bool seam_b, bool walls, int y0, int y1,
@@ -170,7 +171,7 @@ __device__ __forceinline__ void march_step(March<K> &m, const Strip &a, const Co
         const float2(&here)[8] = m.w[l - 1][mod3(P - l)];        // row r
         const float2(&above)[8] = m.w[l - 1][mod3(P - l + 1)];   // row r + 1
         float2 d[8];
-        pull_level<SEAM>(below, here, above, k, seam_a, seam_b, walls, r, a.ny, d);
+        pull_level<SEAM, WALLS>(below, here, above, k, seam_a, seam_b, walls, r, a.ny, d);
         collide_f32<float2>(d, k);
         if (l < K) {
 #pragma unroll
@@ -188,9 +189,10 @@ __device__ __forceinline__ void march_step(March<K> &m, const Strip &a, const Co
 // a.src into a.dst.  H: the halo, even and >= K (a batch keeps one strip
 // layout for launches of fewer steps).  SEAM: the lattice has the seam
 // gradient (without it no jump is added: fewer instructions per level).
+// WALLS = false: y is periodic (the wall rule is left out of the code).
 // Every lane of the warp calls it (shuffles); warp_ring is the warp's
 // RING_ELEMS float2 of shared memory.
-template <int K, bool SEAM>
+template <int K, bool SEAM, bool WALLS = true>
 __device__ __forceinline__ void run_strip(const Strip &a, const Coef<float> &k, int tx, int sg,
                                           int H, float2 *warp_ring) {
     const int S = stride_of(H);
@@ -202,7 +204,7 @@ __device__ __forceinline__ void run_strip(const Strip &a, const Coef<float> &k, 
     const bool grad = a.bc_x == BC_GRADIENT;
     const bool seam_a = grad && xa == 0;          // node a pulls c_x = +1 across the seam
     const bool seam_b = grad && xa + 2 == nx;     // node b pulls c_x = -1 across it
-    const bool walls = a.bc_y == BC_WALLS;
+    const bool walls = WALLS && a.bc_y == BC_WALLS;
     const int y0 = sg * a.seg_rows;
     const int y1 = min(y0 + a.seg_rows, a.ny);
     const int s_lo = walls ? max(y0 - K, 0) : y0 - K;
@@ -228,16 +230,16 @@ __device__ __forceinline__ void run_strip(const Strip &a, const Coef<float> &k, 
     // a position, so no slot keeps a value past its third position
     int s = s_lo;
     for (; s + 2 <= s_end; s += 3) {
-        march_step<K, 0, SEAM>(m, a, k, s, xa, out_lane, seam_a, seam_b, walls, y0, y1, s_lo, s_load_hi);
-        march_step<K, 1, SEAM>(m, a, k, s + 1, xa, out_lane, seam_a, seam_b, walls, y0, y1,
+        march_step<K, 0, SEAM, WALLS>(m, a, k, s, xa, out_lane, seam_a, seam_b, walls, y0, y1, s_lo, s_load_hi);
+        march_step<K, 1, SEAM, WALLS>(m, a, k, s + 1, xa, out_lane, seam_a, seam_b, walls, y0, y1,
                          s_lo, s_load_hi);
-        march_step<K, 2, SEAM>(m, a, k, s + 2, xa, out_lane, seam_a, seam_b, walls, y0, y1,
+        march_step<K, 2, SEAM, WALLS>(m, a, k, s + 2, xa, out_lane, seam_a, seam_b, walls, y0, y1,
                          s_lo, s_load_hi);
     }
     if (s <= s_end)
-        march_step<K, 0, SEAM>(m, a, k, s, xa, out_lane, seam_a, seam_b, walls, y0, y1, s_lo, s_load_hi);
+        march_step<K, 0, SEAM, WALLS>(m, a, k, s, xa, out_lane, seam_a, seam_b, walls, y0, y1, s_lo, s_load_hi);
     if (s + 1 <= s_end)
-        march_step<K, 1, SEAM>(m, a, k, s + 1, xa, out_lane, seam_a, seam_b, walls, y0, y1,
+        march_step<K, 1, SEAM, WALLS>(m, a, k, s + 1, xa, out_lane, seam_a, seam_b, walls, y0, y1,
                          s_lo, s_load_hi);
     cp_wait<0>();          // nothing of this march left in flight
 }

@@ -117,7 +117,7 @@ struct March16 {
 };
 
 // One march position s with s - s_lo = P (mod 3).
-template <typename T, int K, int P, bool SEAM, bool SR>
+template <typename T, int K, int P, bool SEAM, bool SR, bool WALLS>
 __device__ __forceinline__ void march_step16(March16<K> &m, const Strip16 &a,
                                              const Coef<float> &k, int s, int lane, int xa,
                                              int b, bool rec_lane, bool out_lane, bool seam_a,
@@ -141,7 +141,7 @@ __device__ __forceinline__ void march_step16(March16<K> &m, const Strip16 &a,
     for (int l = 1; l <= K; ++l) {
         const int r = s - l;
         float2 d[8];
-        wave::pull_level<SEAM>(m.w[l - 1][mod3(P - l - 1)], m.w[l - 1][mod3(P - l)],
+        wave::pull_level<SEAM, WALLS>(m.w[l - 1][mod3(P - l - 1)], m.w[l - 1][mod3(P - l)],
                                m.w[l - 1][mod3(P - l + 1)], k, seam_a, seam_b, walls, r, a.ny,
                                d);
         float2 rho, mx, my;
@@ -179,7 +179,8 @@ __device__ __forceinline__ void march_step16(March16<K> &m, const Strip16 &a,
 // written columns, tx S .. tx S + 55 with S = 56, are whole tiles.
 constexpr int H16 = 4;
 
-template <typename T, int K, bool SEAM, bool SR>
+// WALLS = false: y is periodic (the wall rule is left out of the code).
+template <typename T, int K, bool SEAM, bool SR, bool WALLS>
 __device__ __forceinline__ void run_strip16(const Strip16 &a, const Coef<float> &k, int tx,
                                             int sg, unsigned *warp_ring) {
     static_assert(K <= H16, "the halo must cover the steps");
@@ -202,7 +203,7 @@ __device__ __forceinline__ void run_strip16(const Strip16 &a, const Coef<float> 
     const bool grad = a.bc_x == BC_GRADIENT;
     const bool seam_a = grad && xa == 0;
     const bool seam_b = grad && xa + 2 == nx;
-    const bool walls = a.bc_y == BC_WALLS;
+    const bool walls = WALLS && a.bc_y == BC_WALLS;
     const int y0 = sg * a.seg_rows;
     const int y1 = min(y0 + a.seg_rows, a.ny);
     const int s_lo = walls ? max(y0 - K, 0) : y0 - K;
@@ -225,32 +226,32 @@ __device__ __forceinline__ void run_strip16(const Strip16 &a, const Coef<float> 
         stage_row16<T>(m.ring, lane, a, k, xa, s_lo + j, j, s_lo + j <= s_load_hi);
     int s = s_lo;
     for (; s + 2 <= s_end; s += 3) {
-        march_step16<T, K, 0, SEAM, SR>(m, a, k, s, lane, xa, b, rec_lane, out_lane, seam_a,
+        march_step16<T, K, 0, SEAM, SR, WALLS>(m, a, k, s, lane, xa, b, rec_lane, out_lane, seam_a,
                                         seam_b, walls, y0, y1, s_lo, s_load_hi);
-        march_step16<T, K, 1, SEAM, SR>(m, a, k, s + 1, lane, xa, b, rec_lane, out_lane, seam_a,
+        march_step16<T, K, 1, SEAM, SR, WALLS>(m, a, k, s + 1, lane, xa, b, rec_lane, out_lane, seam_a,
                                         seam_b, walls, y0, y1, s_lo, s_load_hi);
-        march_step16<T, K, 2, SEAM, SR>(m, a, k, s + 2, lane, xa, b, rec_lane, out_lane, seam_a,
+        march_step16<T, K, 2, SEAM, SR, WALLS>(m, a, k, s + 2, lane, xa, b, rec_lane, out_lane, seam_a,
                                         seam_b, walls, y0, y1, s_lo, s_load_hi);
     }
     if (s <= s_end)
-        march_step16<T, K, 0, SEAM, SR>(m, a, k, s, lane, xa, b, rec_lane, out_lane, seam_a,
+        march_step16<T, K, 0, SEAM, SR, WALLS>(m, a, k, s, lane, xa, b, rec_lane, out_lane, seam_a,
                                         seam_b, walls, y0, y1, s_lo, s_load_hi);
     if (s + 1 <= s_end)
-        march_step16<T, K, 1, SEAM, SR>(m, a, k, s + 1, lane, xa, b, rec_lane, out_lane, seam_a,
+        march_step16<T, K, 1, SEAM, SR, WALLS>(m, a, k, s + 1, lane, xa, b, rec_lane, out_lane, seam_a,
                                         seam_b, walls, y0, y1, s_lo, s_load_hi);
     wave::cp_wait<0>();
 }
 
-// 12 warps per SM: the 4-step march fits 168 registers with a few bytes of
-// spills (219 -> 230 GLUPS for FP16 at 8192^2 with blocks of 4 warps);
-// fewer steps fit without.
-template <typename T, int K, bool SEAM, bool SR>
+// 12 warps per SM: the 4-step march fits 168 registers (with blocks of 4
+// warps and a few bytes of spills this took FP16 at 8192^2 from 219 to 230
+// GLUPS); fewer steps fit in fewer.
+template <typename T, int K, bool SEAM, bool SR, bool WALLS>
 __global__ void __launch_bounds__(W16_WARPS * 32, 12 / W16_WARPS)
 step_wave16(const Strip16 a, const Coef<float> k, int tiles_x, long long items) {
     extern __shared__ unsigned w16_ring[];
     const long long item = (long long)blockIdx.x * W16_WARPS + (threadIdx.x >> 5);
     if (item >= items) return;                   // whole warps leave together
-    run_strip16<T, K, SEAM, SR>(a, k, int(item % tiles_x), int(item / tiles_x),
+    run_strip16<T, K, SEAM, SR, WALLS>(a, k, int(item % tiles_x), int(item / tiles_x),
                                 w16_ring + (threadIdx.x >> 5) * W16_RING * W16_SLOT_WORDS);
 }
 
@@ -262,16 +263,23 @@ cudaError_t launch16_k(const Strip16 &a, const Coef<float> &k, cudaStream_t stre
     const long long items = (long long)tiles_x * segs;
     const long long blocks = (items + W16_WARPS - 1) / W16_WARPS;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const bool seam = a.bc_x == BC_GRADIENT;
+    const bool seam = a.bc_x == BC_GRADIENT, walls = a.bc_y == BC_WALLS;
     const unsigned g = (unsigned)blocks;
+    constexpr int NT = W16_WARPS * 32;
+    // stochastic rounding (opt-in) keeps the wall test at run time; the
+    // nearest-rounding marches leave the wall rule out on periodic y
     if (seam && k.stochastic)
-        step_wave16<T, K, true, true><<<g, W16_WARPS * 32, W16_SMEM, stream>>>(a, k, tiles_x, items);
-    else if (seam)
-        step_wave16<T, K, true, false><<<g, W16_WARPS * 32, W16_SMEM, stream>>>(a, k, tiles_x, items);
+        step_wave16<T, K, true, true, true><<<g, NT, W16_SMEM, stream>>>(a, k, tiles_x, items);
     else if (k.stochastic)
-        step_wave16<T, K, false, true><<<g, W16_WARPS * 32, W16_SMEM, stream>>>(a, k, tiles_x, items);
+        step_wave16<T, K, false, true, true><<<g, NT, W16_SMEM, stream>>>(a, k, tiles_x, items);
+    else if (seam && walls)
+        step_wave16<T, K, true, false, true><<<g, NT, W16_SMEM, stream>>>(a, k, tiles_x, items);
+    else if (seam)
+        step_wave16<T, K, true, false, false><<<g, NT, W16_SMEM, stream>>>(a, k, tiles_x, items);
+    else if (walls)
+        step_wave16<T, K, false, false, true><<<g, NT, W16_SMEM, stream>>>(a, k, tiles_x, items);
     else
-        step_wave16<T, K, false, false><<<g, W16_WARPS * 32, W16_SMEM, stream>>>(a, k, tiles_x, items);
+        step_wave16<T, K, false, false, false><<<g, NT, W16_SMEM, stream>>>(a, k, tiles_x, items);
     return cudaGetLastError();
 }
 
