@@ -124,8 +124,9 @@ typedef enum {
 typedef enum {
     LBM_KERNEL_AUTO = 0,     /* up to 16384 nodes: resident for LBM_FP32,     */
                              /* scalar for LBM_FP64; from 2^24 nodes (nx >=   */
-                             /* 256) wave where it applies (4 steps per       */
-                             /* launch, 256-row segments); else               */
+                             /* 256) wave where it applies (FP32: 5 steps     */
+                             /* per launch, 128-row segments; 16-bit: 4 and   */
+                             /* 256); else                                    */
                              /* vector when nx allows, else scalar            */
                              /* (lbm_autotune times the candidates)           */
     LBM_KERNEL_SCALAR = 1,   /* one thread per node; any nx                   */

@@ -398,17 +398,19 @@ int resolve_kernel(lbm_ctx *c, int requested) {
     }
     if (requested == KERNEL_AUTO) {
         // without timing (lbm_autotune times them): large lattices the
-        // multi-step kernel where it applies (4 steps per launch, 256-row
-        // segments: FP32 320 against 106, FP16 230 against 177 GLUPS at
-        // 8192^2; from 16 M nodes its strip-segments fill the GPU), else
+        // multi-step kernel where it applies (FP32: 5 steps per launch,
+        // 128-row segments, 424 against 105 GLUPS at 8192^2; 16-bit: 4
+        // steps, 256-row segments, 340 against 171; from 16 M nodes its
+        // strip-segments fill the GPU), else
         // the vector kernel, the fastest single-step
         // kernel measured at 8192^2 for every storage kind (FP32 6.7, 16-bit
         // 6.5 TB/s against the staged kernel's 5.7 and 6.0), with the least
         // set-up for small, launch-latency bound lattices
         if (c->plane >= WAVE_AUTO_NODES && c->nx >= 256 &&
             wave_supported(c->precision, c->nx, c->ny, c->bc_x, c->bc_y)) {
-            c->wave_steps = 4;
-            c->wave_rows = 256;
+            const bool fp32 = c->precision == PREC_FP32;
+            c->wave_steps = fp32 ? 5 : 4;
+            c->wave_rows = fp32 ? 128 : 256;
             return KERNEL_WAVE;
         }
         return vec_ok ? KERNEL_VECTOR : KERNEL_SCALAR;
